@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Pauli-rotation throughput on GB300: rotations/s at n = 24, HBM fraction, and
+the speedup over the gate-decomposed path on the same GPU.
+
+Workload (one step): a seeded Jordan-Wigner-shaped Hamiltonian on n = 24 qubits
+with 2000 terms, 10 first-order Trotter steps at dt = 0.05 (20,000 rotations),
+applied to the Hartree-Fock state with 12 electrons, followed by the FP64
+energy <H> and norm.  Synthetic data: the chemistry Hamiltonians the paper
+measures are not available.
+
+Arms:
+  default            the library (plan compiled once; per step: basis state,
+                     all fused passes, FP64 <H>); e2e repeats the step through
+                     the C ABI with host buffers (state upload from pinned
+                     memory, rotation list planned and uploaded per call,
+                     final state and energy read back).
+  --impl reference   the FP64 CPU oracle (gate-decomposed), on a bounded
+                     sample of the same rotation list per step.
+
+Multi-GPU (torchrun): every rank runs an independent replica (the state does
+not shard on one-GPU machines); value = all ranks' rotations / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2602_09020_gb300 import synth  # noqa: E402
+
+METRIC = "Pauli rotations/s at n=24 & HBM fraction; speedup vs gate-decomposed, same GPU"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--n", type=int, default=24)
+    ap.add_argument("--terms", type=int, default=2000)
+    ap.add_argument("--trotter-steps", type=int, default=10)
+    ap.add_argument("--dt", type=float, default=0.05)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--fusion-depth", type=int, default=-1)
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="only the timed steps (for profiler launch lists)")
+    return ap.parse_args()
+
+
+def workload_name(a) -> str:
+    return (f"JW-shaped H, n={a.n}, {a.terms} terms, {a.trotter_steps} first-order Trotter steps "
+            f"at dt={a.dt} ({a.terms * a.trotter_steps} rotations), HF state, then FP64 <H>")
+
+
+def config_dict(a, dtype) -> dict:
+    return {"workload": workload_name(a), "n_qubits": a.n, "terms": a.terms, "trotter_steps": a.trotter_steps,
+            "order": 1, "dt": a.dt, "seed": a.seed, "state": dtype,
+            "rotations_per_step": a.terms * a.trotter_steps,
+            "l2": "inputs > L2 for c128; L2 flushed (512 MB write) between timed steps",
+            "parallelism": "replicas"}
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def ncu_traffic() -> dict:
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return {}
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def mhz(s):
+            try:
+                return float(s.split()[0])
+            except (ValueError, IndexError):
+                return None
+        sm = [mhz(r[1]) for r in rows if mhz(r[1]) is not None]
+        mx = [mhz(r[2]) for r in rows if mhz(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = [nm for i, nm in enumerate(names) if any(r[5 + i].lower().startswith("active") for r in rows)]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_rate(n, rx, rz, rt, seconds: float, basis: int):
+    """Apply rotations with the oracle until `seconds` pass; returns (rot/s, count, threads, s)."""
+    import oracle
+    psi = oracle.basis_state(n, basis)
+    t0 = time.perf_counter()
+    k = 0
+    while k < len(rt) and (k < 2 or time.perf_counter() - t0 < seconds):
+        oracle.apply_rotation(psi, n, int(rx[k]), int(rz[k]), float(rt[k]))
+        k += 1
+    el = time.perf_counter() - t0
+    return k / el, k, oracle.num_threads(), el
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    ham = synth.jw_hamiltonian(a.n, a.terms, a.seed)
+    rx, rz, rt = oracle.trotter_rotations(ham.x, ham.z, ham.c, a.dt, a.trotter_steps, 1)
+    basis = synth.hartree_fock_index(a.n // 2)
+    # calibrate a sample so that warmup + steps take about two minutes
+    r1, _, threads, _ = oracle_rate(a.n, rx, rz, rt, 2.0, basis)
+    per_step = max(2, int(r1 * 120.0 / max(1, a.steps + a.warmup)))
+    per_step = min(per_step, len(rt))
+    times = []
+    for s in range(a.warmup + a.steps):
+        t0 = time.perf_counter()
+        psi = oracle.basis_state(a.n, basis)
+        oracle.apply_rotations(psi, a.n, rx[:per_step], rz[:per_step], rt[:per_step])
+        el = time.perf_counter() - t0
+        if s >= a.warmup:
+            times.append(el)
+    ms = 1000.0 * statistics.mean(times)
+    value = per_step / (ms / 1000.0)
+    sample = f"first {per_step} of {len(rt)} rotations per step (n={a.n}, complex128, gate-decomposed)"
+    line = {"metric": METRIC, "value": value, "unit": "rotations/s", "impl": "reference", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": config_dict(a, "c128"),
+            "cpu_baseline": {"value": value, "unit": "rotations/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "rotations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(a):
+    import torch
+    from paper_2602_09020_gb300 import capi
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    sh = int(stream.cuda_stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ham = synth.jw_hamiltonian(a.n, a.terms, a.seed)
+    rx, rz, rt = capi.trotter_expand(ham.x, ham.z, ham.c, a.dt, a.trotter_steps, 1, False)
+    R = len(rt)
+    basis = synth.hartree_fock_index(a.n // 2)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    pk = peaks()
+
+    def measure(dtype: str, steps: int, warmup: int, trace: bool, clocks: Clocks = None):
+        t0 = time.perf_counter()
+        plan = capi.plan_create(a.n, dtype, rx, rz, rt, a.fusion_depth, sh)
+        plan_ms = 1000.0 * (time.perf_counter() - t0)
+        nrot, nruns, ndiag = capi.plan_stats(plan)
+        sv = capi.sv_alloc(a.n, dtype, sh)
+        out = {}
+
+        def step():
+            capi.sv_set_basis_state(sv, basis)
+            capi.plan_apply(sv, plan)
+            out["energy"], out["norm2"] = capi.expval_pauli_sum(sv, ham.x, ham.z, ham.c)
+
+        for _ in range(warmup):
+            step()
+        barrier()
+        if clocks:
+            clocks.start()
+        if trace:
+            capi.sv_trace_start(sv)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        barrier()
+        rows = capi.sv_trace_stop(sv) if trace else {}
+        ck = clocks.stop() if clocks else None
+        ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+        capi.sv_free(sv)
+        capi.plan_free(plan)
+        return {"ms": ms, "plan_ms": plan_ms, "runs": nruns, "diag_runs": ndiag, "nrot": nrot,
+                "trace": rows, "clocks": ck, "energy": out["energy"], "norm2": out["norm2"]}
+
+    def roofline(rows: dict, steps: int):
+        if not rows:
+            return None, 0
+        name = max(rows, key=lambda k: rows[k][1])
+        launches, tot_ms, by = rows[name]
+        achieved = by / (tot_ms / 1000.0) / 1e9
+        traffic = ncu_traffic().get(f"{name}/{a.dtype}/n{a.n}")
+        return ({"kernel": name, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                 "frac": achieved / pk["hbm_gbs"], "peak_source": pk["source"],
+                 "traffic": traffic, "launches_per_step": launches / steps,
+                 "ms_per_launch": tot_ms / launches,
+                 "algorithmic_bytes_per_launch": by / launches},
+                sum(r[0] for r in rows.values()))
+
+    clocks = Clocks(dev)
+    main = measure(a.dtype, a.steps, a.warmup, True, clocks)
+    ms_step = statistics.mean(main["ms"])
+    ms_max = max_over_ranks(ms_step)
+    value = world * R / (ms_max / 1000.0)
+    roof, launches = roofline(main["trace"], a.steps)
+    s_bytes = 16 if a.dtype == "c128" else 8
+    sweep_bytes = 2.0 * s_bytes * (1 << a.n)
+
+    extras = {}
+    if not a.skip_extras:
+        # the other precision, device-timed
+        other = "c128" if a.dtype == "c64" else "c64"
+        o = measure(other, max(1, min(a.steps, 2)), 1, True)
+        o_roof, _ = roofline(o["trace"], max(1, min(a.steps, 2)))
+        extras[other] = {"value": R / (statistics.mean(o["ms"]) / 1000.0), "ms_per_step": statistics.mean(o["ms"]),
+                         "passes_per_step": o["runs"], "energy": o["energy"], "roofline": o_roof}
+        # gate-decomposed path on the same GPU, same dtype: a strided sample of one Trotter step
+        sample = slice(0, a.terms, 4)
+        gx, gz, gt = rx[sample], rz[sample], rt[sample]
+        svg = capi.sv_alloc(a.n, a.dtype, sh)
+        capi.sv_set_basis_state(svg, basis)
+        capi.apply_pauli_rotations_gates(svg, gx[:20], gz[:20], gt[:20])  # warm
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ngates = capi.apply_pauli_rotations_gates(svg, gx, gz, gt)
+        e1.record(stream)
+        barrier()
+        g_ms = e0.elapsed_time(e1)
+        capi.sv_free(svg)
+        g_rate = len(gt) / (g_ms / 1000.0)
+        extras["gate_decomposed"] = {"rotations": len(gt), "gates": ngates, "ms": g_ms,
+                                     "rotations_per_s": g_rate, "speedup": (R / (ms_step / 1000.0)) / g_rate,
+                                     "sample": "every 4th rotation of the first Trotter step"}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not a.skip_extras:
+        amp_dt = torch.complex128 if a.dtype == "c128" else torch.complex64
+        h_in = torch.zeros(1 << a.n, dtype=amp_dt, pin_memory=True)
+        h_in[basis] = 1.0
+        h_out = torch.empty(1 << a.n, dtype=amp_dt, pin_memory=True)
+        sv = capi.sv_alloc(a.n, a.dtype, sh)
+        lib = capi.lib()
+        xs, zs, ts = np.ascontiguousarray(rx), np.ascontiguousarray(rz), np.ascontiguousarray(rt)
+        e_out, n_out = ctypes.c_double(), ctypes.c_double()
+
+        def e2e_step():
+            capi._check(lib.sv_from_host(sv, h_in.data_ptr()))
+            capi._check(lib.apply_pauli_rotations(sv, xs.ctypes.data, zs.ctypes.data, ts.ctypes.data, R))
+            capi._check(lib.expval_pauli_sum(sv, ham.x.ctypes.data, ham.z.ctypes.data, ham.c.ctypes.data,
+                                             len(ham.c), ctypes.byref(e_out), ctypes.byref(n_out)))
+            capi._check(lib.sv_to_host(sv, h_out.data_ptr(), 1))
+
+        e2e_step()
+        barrier()
+        n_e2e = max(1, min(a.steps, 2))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        barrier()
+        el = (time.perf_counter() - t0) / n_e2e
+        el = max_over_ranks(el)
+        capi.sv_free(sv)
+        state_bytes = s_bytes << a.n
+        e2e = {"value": world * R / el, "unit": "rotations/s",
+               "h2d_bytes_per_step": state_bytes + R * 24 + len(ham.c) * 24,
+               "d2h_bytes_per_step": state_bytes + 16, "ms_per_step": 1000.0 * el}
+
+    cpu = None
+    if world == 1 and not a.skip_extras:
+        rate, k, threads, el = oracle_rate(a.n, rx, rz, rt, 12.0, basis)
+        cpu = {"value": rate, "unit": "rotations/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {k} rotations of the step at n={a.n}, complex128 gate-decomposed ({el:.1f} s)"}
+
+    if rank != 0:
+        return 0
+    passes = main["runs"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "rotations/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": a.dtype, "data": "synthetic (seeded JW-shaped Hamiltonian)",
+        "config": config_dict(a, a.dtype),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": main["clocks"],
+        "passes_per_step": passes, "diag_passes_per_step": main["diag_runs"],
+        "rotations_per_pass": main["nrot"] / max(1, passes),
+        "effective_gbs": R * sweep_bytes / (ms_step / 1000.0) / 1e9,
+        "rescaled_runtime_s": (ms_step / 1000.0) / (R * (1 << a.n)),
+        "plan_ms": main["plan_ms"], "energy": main["energy"], "norm2": main["norm2"],
+        "kernels": {k: {"launches": v[0], "ms": v[1], "gbs": (v[2] / (v[1] / 1000.0) / 1e9) if v[1] else None}
+                    for k, v in main["trace"].items()},
+    }
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,241 @@
+/*
+ * paulirot.h -- C ABI of the GB300 Pauli-rotation statevector library
+ * (libpaulirot.so, CUDA kernels for sm_103a plus host C++).
+ *
+ * What it computes (arXiv 2602.09020):
+ *   * R_P(theta) = exp(-i theta/2 P) on an n-qubit statevector, every rotation
+ *     pairing amplitude k with f_P(k) = k XOR x and the phase
+ *     i^{nY} (-1)^{popc(k & z)} (Sec. "Multi-qubit rotations in a fullstate
+ *     simulator" and App. "Amplitude update rule for multi-qubit rotations").
+ *   * Pauli gates kept in a Pauli frame Q, so that the represented state is
+ *     |psi> = Q |phi> and a rotation about P acts on |phi> about Q^dag P Q =
+ *     +-P (Sec. "Pauli Frame as a Lookup Table", Eq. single_to_multirot, with
+ *     the frame restricted to Pauli gates).
+ *   * <psi|sum_j c_j P_j|psi> = sum_j c_j <phi|Q^dag P_j Q|phi>
+ *     (Sec. "Extraction of Expectation Values", Eqs. Fmap and chfsexp).
+ *   * First-order Trotter products, Eq. (trotter), and a symmetric
+ *     second-order product (not in the paper; see trotter_expand).
+ *   * dE/dtheta_j of E = <psi|H|psi> by an adjoint sweep (not in the paper).
+ *
+ * Conventions
+ *   * qubit j is bit j of the amplitude index (qubit 0 least significant);
+ *   * a Pauli string is a pair of uint64 masks (x, z): X on bits x & ~z,
+ *     Z on z & ~x, Y on x & z; bits >= n must be zero;
+ *   * theta is the angle of exp(-i theta/2 P), FP64;
+ *   * amplitudes are interleaved (re, im): SV_C128 = 2 x double per amplitude,
+ *     SV_C64 = 2 x float.  Angle trigonometry and every reduction are FP64 in
+ *     both modes.
+ *
+ * Errors: every function returns an int status (SV_OK = 0, negative on
+ * failure) and never aborts or exits.  sv_last_error() gives a thread-local
+ * message for the last failure on the calling thread.
+ *
+ * Ownership: host arrays passed in are read (or written) before the call
+ * returns and stay owned by the caller.  Device memory made by sv_alloc and
+ * all internal scratch belong to the library and are released by sv_free.
+ * sv_wrap borrows caller memory, which must outlive the handle.
+ *
+ * Streams: all device work of a handle is enqueued on its CUDA stream
+ * (cudaStream_t passed as void*, NULL = legacy default stream).  Calls that
+ * return host values (expval_pauli_sum, rotation_grads, sv_to_host, ...)
+ * synchronise that stream before returning.
+ */
+#ifndef PAULIROT_H
+#define PAULIROT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define SV_OK 0
+#define SV_EINVAL (-1)       /* bad argument: null pointer, mask bit >= n, NaN/Inf angle, ... */
+#define SV_ENOMEM (-2)       /* device or host allocation failed, or n too large */
+#define SV_ECUDA (-3)        /* a CUDA runtime call failed (message has the CUDA error) */
+#define SV_ETIMEOUT (-4)     /* a bounded device wait gave up (batched launch) */
+#define SV_EUNSUPPORTED (-5) /* valid request this build does not handle */
+
+/* ---- amplitude types ------------------------------------------------------- */
+#define SV_C128 0 /* complex128: 16 bytes per amplitude, n <= 33 */
+#define SV_C64 1  /* complex64:   8 bytes per amplitude, n <= 34 */
+
+typedef struct sv_state sv_state; /* opaque: amplitudes, n, dtype, stream, frame, scratch */
+typedef struct sv_plan sv_plan;   /* opaque: a rotation list compiled into fused runs */
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char *sv_last_error(void);
+
+/* Library version, (major << 16) | minor. */
+int sv_version(void);
+
+/* ---- statevector handles ----------------------------------------------------- */
+
+/* Allocate a 2^n-amplitude state on the current CUDA device, set to |0..0>,
+ * frame = identity.  dtype is SV_C128 or SV_C64.  SV_ENOMEM if n exceeds the
+ * dtype's limit or the allocation fails (nothing is left allocated). */
+int sv_alloc(sv_state **out, int n_qubits, int dtype, void *cuda_stream);
+
+/* Wrap caller-owned device memory of 2^n amplitudes (16-byte aligned); the
+ * contents are taken as |phi> with the identity frame.  Not freed by sv_free. */
+int sv_wrap(sv_state **out, void *dev_amps, int n_qubits, int dtype, void *cuda_stream);
+
+/* Release the handle (and the amplitudes if sv_alloc made them). NULL is OK. */
+int sv_free(sv_state *sv);
+
+/* Change the stream used by later calls on this handle. */
+int sv_set_stream(sv_state *sv, void *cuda_stream);
+
+/* Device pointer to the stored amplitudes |phi> (not materialised). */
+int sv_device_ptr(sv_state *sv, void **out);
+
+/* Query n and dtype. */
+int sv_info(sv_state *sv, int *n_qubits, int *dtype);
+
+/* |phi> = |k>, frame = identity. */
+int sv_set_basis_state(sv_state *sv, uint64_t k);
+
+/* |phi> = host amplitudes (2^n of the handle's dtype), frame = identity. */
+int sv_from_host(sv_state *sv, const void *host_amps);
+
+/* Copy amplitudes to host memory (2^n of the handle's dtype).  With
+ * materialize_frame != 0 the frame is first applied to the device state (see
+ * sv_materialize), so the copy is |psi>; with 0 the copy is |phi>. */
+int sv_to_host(sv_state *sv, void *host_amps, int materialize_frame);
+
+/* Apply the frame Q to the stored amplitudes in place (|phi> <- Q|phi>, one
+ * pass), then reset the frame: the represented state |psi> is unchanged
+ * (paper, Sec. "Extraction of Expectation Values": (F, Phi) -> (F_origin, Psi),
+ * here for a Pauli-only frame with its exact phase). */
+int sv_materialize(sv_state *sv);
+
+/* Copy state and frame of src into dst (same n and dtype). */
+int sv_copy(sv_state *dst, const sv_state *src);
+
+/* ---- Pauli frame (host only, O(1) per call) --------------------------------- */
+
+/* Reset the frame to the identity. */
+int frame_reset(sv_state *sv);
+
+/* Apply the Pauli gate pauli ('X', 'Y' or 'Z') on qubit to the represented
+ * state by updating the frame only: Q <- G Q with the exact phase (paper,
+ * Fig. "CFHS gate flow": Clifford gates update F, here Pauli gates). */
+int frame_apply_pauli(sv_state *sv, char pauli, int qubit);
+
+/* Read the frame Q = i^phase X^xq Z^zq (phase in 0..3). */
+int frame_get(sv_state *sv, uint64_t *xq, uint64_t *zq, int *phase);
+
+/* ---- rotations ----------------------------------------------------------------- */
+
+/* Apply R_{P_0}(angles[0]) first, then P_1, ... to the represented state.
+ * Host arrays of length count.  Each rotation is rewritten by the frame
+ * (sign flip where P anticommutes with Q), the list is compiled into fused
+ * runs (same work as plan_create with fusion_depth = -1) and launched on the
+ * handle's stream.  Returns before the device work finishes. */
+int apply_pauli_rotations(sv_state *sv, const uint64_t *x, const uint64_t *z,
+                          const double *angles, size_t count);
+
+/* Compile a rotation list once for states of n qubits and this dtype.
+ * fusion_depth = maximum dimension of the span of x-masks fused into one
+ * pass (0..5; -1 = tuned default for the dtype).  The plan's device buffers
+ * are uploaded on cuda_stream; plan_apply then launches kernels only (no
+ * host-to-device copy), so it can be captured into a CUDA graph. */
+int plan_create(sv_plan **out, int n_qubits, int dtype, const uint64_t *x, const uint64_t *z,
+                const double *angles, size_t count, int fusion_depth, void *cuda_stream);
+
+/* Apply a plan to a state (same n and dtype).  The frame signs are taken from
+ * the handle's frame at call time (a captured graph replays the frame it was
+ * captured with).  Updates the handle's frame on the host. */
+int plan_apply(sv_state *sv, sv_plan *plan);
+
+int plan_free(sv_plan *plan);
+
+/* Plan statistics: number of rotations (after dropping identities), number
+ * of fused runs (= HBM passes), of which diagonal phase-sum runs. */
+int plan_stats(const sv_plan *plan, size_t *n_rotations, size_t *n_runs, size_t *n_diag_runs);
+
+/* ---- Trotter products (host) ----------------------------------------------------- */
+
+/* Expand H = sum_j c_j P_j (T terms) into a rotation list.
+ * order 1, Eq. (trotter): per step exp(-i c_j P_j dt) for j = 1..T, theta = 2 c_j dt.
+ * order 2 (symmetric, not in the paper): per step theta = c_j dt for j = 1..T then
+ * for j = T..1.  With merge != 0 neighbouring rotations about the same string
+ * are merged into one (exact), which for order 2 joins the middle pair and
+ * the pair across step boundaries.  Writes at most cap entries; *out_count is
+ * the full length (call with cap = 0 to size the arrays). */
+int trotter_expand(const uint64_t *x, const uint64_t *z, const double *c, size_t n_terms,
+                   double dt, int steps, int order, int merge, uint64_t *out_x, uint64_t *out_z,
+                   double *out_theta, size_t cap, size_t *out_count);
+
+/* ---- reductions (FP64) ----------------------------------------------------------- */
+
+/* out_energy = <psi|sum_j c_j P_j|psi> for the represented state, FP64.
+ * out_norm2 (nullable) = <psi|psi>.  Terms are grouped by x-mask and several
+ * groups are evaluated per pass; partial sums are reduced in a fixed order,
+ * so repeated calls give bitwise-equal results. */
+int expval_pauli_sum(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *coeff,
+                     size_t count, double *out_energy, double *out_norm2);
+
+/* dst <- sum_j c_j P_j applied to src's represented state (dst gets the
+ * identity frame).  Same n and dtype; dst must not be src. */
+int apply_pauli_sum(sv_state *dst, sv_state *src, const uint64_t *x, const uint64_t *z,
+                    const double *coeff, size_t count);
+
+/* ---- adjoint gradient (not in the paper) -------------------------------------------- */
+
+/* E = <psi|H|psi> with psi = R_{n_rot-1} ... R_0 psi0 (psi0 = the represented
+ * state of the handle, left unchanged), and out_grads[j] = dE/dtheta_j for all
+ * j, FP64.  Adjoint method: lambda = H psi, then for j = n_rot-1 .. 0:
+ * g_j = Im <lambda|P_j|phi_j>, phi <- R_j^dag phi, lambda <- R_j^dag lambda.
+ * Uses two temporary states of psi0's size. */
+int rotation_grads(sv_state *psi0, const uint64_t *x, const uint64_t *z, const double *angles,
+                   size_t n_rot, const uint64_t *hx, const uint64_t *hz, const double *hc,
+                   size_t n_terms, double *out_energy, double *out_grads);
+
+/* ---- gate-decomposed comparison path -------------------------------------------------- */
+
+/* The same rotations applied the textbook way, one HBM pass per gate: basis
+ * change per X/Y qubit (H, or Sdg then H), a CNOT ladder over the support,
+ * Rz on its top qubit, the ladder and basis change undone (paper, Sec.
+ * "Preliminaries of Hamiltonian Simulation", CNOT-staircase figure, 2(k-1)
+ * CNOTs).  Frame signs are applied as in apply_pauli_rotations.  Used as the
+ * same-GPU baseline; *out_gates (nullable) receives the number of gate
+ * kernels launched. */
+int apply_pauli_rotations_gates(sv_state *sv, const uint64_t *x, const uint64_t *z,
+                                const double *angles, size_t count, size_t *out_gates);
+
+/* ---- batched independent states (not in the paper) --------------------------------------- */
+
+/* Apply plans[i] to states[i] for i < count (independent problems of uneven
+ * sizes, all SV_C64 or all SV_C128) in one persistent launch on the stream of
+ * states[0].  With use_graph != 0 the launch is captured into a CUDA graph
+ * once per (states, plans) set and replayed.  Device waits are bounded: a
+ * wait that runs out sets an error word and the call returns SV_ETIMEOUT. */
+int batch_run(sv_state **states, sv_plan **plans, size_t count, int use_graph);
+
+/* ---- tracing (not in the paper) --------------------------------------------------------- */
+
+/* One row per kernel name: launches, summed device time and algorithmic HBM
+ * bytes (reads + writes the kernel must make, counted from its inputs). */
+typedef struct sv_trace_row {
+  char name[40];
+  int64_t launches;
+  double total_ms;
+  double bytes;
+} sv_trace_row;
+
+/* Start recording a CUDA event pair around every kernel this handle launches
+ * (on the handle's stream).  Recording adds two event records per launch. */
+int sv_trace_start(sv_state *sv);
+
+/* Stop recording, synchronise the stream and aggregate per kernel name into
+ * rows (at most cap; *n_rows = rows written).  Events are recycled. */
+int sv_trace_stop(sv_state *sv, sv_trace_row *rows, int cap, int *n_rows);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAULIROT_H */

@@ -1,0 +1,308 @@
+"""Thin ctypes binding of libpaulirot.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: masks, angles and coefficients are converted to
+contiguous numpy arrays, handles are passed through, status codes are turned
+into :class:`PauliRotError`.  PyTorch is used only to own device memory and to
+provide the current CUDA stream (see :class:`StateVector`).
+
+If the library is missing it is built from ``csrc/`` with nvcc; if that is not
+possible an ImportError-like :class:`PauliRotError` is raised -- there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_ETIMEOUT, SV_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+SV_C128, SV_C64 = 0, 1
+_DTYPES = {"c128": SV_C128, "complex128": SV_C128, SV_C128: SV_C128,
+           "c64": SV_C64, "complex64": SV_C64, SV_C64: SV_C64}
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+class PauliRotError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def dtype_code(dtype) -> int:
+    try:
+        return _DTYPES[dtype]
+    except KeyError:
+        raise ValueError(f"dtype must be 'c128' or 'c64', got {dtype!r}") from None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load (building first if needed) libpaulirot.so and declare its symbols."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    try:
+        path = _build.build()
+    except Exception as exc:  # no nvcc / compile error: fail loudly
+        raise PauliRotError(SV_EUNSUPPORTED, f"libpaulirot.so is not available: {exc}") from exc
+    L = ctypes.CDLL(path)
+    vp, i, sz, u64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "sv_last_error": ([], ctypes.c_char_p),
+        "sv_version": ([], i),
+        "sv_alloc": ([P(vp), i, i, vp], i),
+        "sv_wrap": ([P(vp), vp, i, i, vp], i),
+        "sv_free": ([vp], i),
+        "sv_set_stream": ([vp, vp], i),
+        "sv_device_ptr": ([vp, P(vp)], i),
+        "sv_info": ([vp, P(i), P(i)], i),
+        "sv_set_basis_state": ([vp, u64], i),
+        "sv_from_host": ([vp, vp], i),
+        "sv_to_host": ([vp, vp, i], i),
+        "sv_materialize": ([vp], i),
+        "sv_copy": ([vp, vp], i),
+        "frame_reset": ([vp], i),
+        "frame_apply_pauli": ([vp, ctypes.c_char, i], i),
+        "frame_get": ([vp, P(u64), P(u64), P(i)], i),
+        "apply_pauli_rotations": ([vp, vp, vp, vp, sz], i),
+        "plan_create": ([P(vp), i, i, vp, vp, vp, sz, i, vp], i),
+        "plan_apply": ([vp, vp], i),
+        "plan_free": ([vp], i),
+        "plan_stats": ([vp, P(sz), P(sz), P(sz)], i),
+        "trotter_expand": ([vp, vp, vp, sz, d, i, i, i, vp, vp, vp, sz, P(sz)], i),
+        "expval_pauli_sum": ([vp, vp, vp, vp, sz, P(d), P(d)], i),
+        "apply_pauli_sum": ([vp, vp, vp, vp, vp, sz], i),
+        "rotation_grads": ([vp, vp, vp, vp, sz, vp, vp, vp, sz, P(d), vp], i),
+        "apply_pauli_rotations_gates": ([vp, vp, vp, vp, sz, P(sz)], i),
+        "batch_run": ([vp, vp, sz, i], i),
+        "sv_trace_start": ([vp], i),
+        "sv_trace_stop": ([vp, vp, i, P(i)], i),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def exported_symbols() -> Sequence[str]:
+    return ["sv_last_error", "sv_version", "sv_alloc", "sv_wrap", "sv_free", "sv_set_stream",
+            "sv_device_ptr", "sv_info", "sv_set_basis_state", "sv_from_host", "sv_to_host",
+            "sv_materialize", "sv_copy", "frame_reset", "frame_apply_pauli", "frame_get",
+            "apply_pauli_rotations", "plan_create", "plan_apply", "plan_free", "plan_stats",
+            "trotter_expand", "expval_pauli_sum", "apply_pauli_sum", "rotation_grads",
+            "apply_pauli_rotations_gates", "batch_run", "sv_trace_start", "sv_trace_stop"]
+
+
+def _check(rc: int) -> None:
+    if rc != SV_OK:
+        msg = lib().sv_last_error()
+        raise PauliRotError(rc, msg.decode() if msg else "")
+
+
+def _u64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint64))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _p(a: np.ndarray) -> Optional[int]:
+    return a.ctypes.data if a.size else None
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    s = getattr(stream, "cuda_stream", None)  # torch.cuda.Stream
+    return int(s) if s else None
+
+
+# ------------------------------------------------------------------ C entry points
+
+def sv_alloc(n_qubits: int, dtype="c128", stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sv_alloc(ctypes.byref(h), int(n_qubits), dtype_code(dtype), _stream(stream)))
+    return h.value
+
+
+def sv_wrap(dev_ptr: int, n_qubits: int, dtype="c128", stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sv_wrap(ctypes.byref(h), int(dev_ptr), int(n_qubits), dtype_code(dtype), _stream(stream)))
+    return h.value
+
+
+def sv_free(sv: int) -> None:
+    _check(lib().sv_free(sv))
+
+
+def sv_set_stream(sv: int, stream) -> None:
+    _check(lib().sv_set_stream(sv, _stream(stream)))
+
+
+def sv_info(sv: int) -> Tuple[int, int]:
+    n, d = ctypes.c_int(), ctypes.c_int()
+    _check(lib().sv_info(sv, ctypes.byref(n), ctypes.byref(d)))
+    return n.value, d.value
+
+
+def sv_set_basis_state(sv: int, k: int) -> None:
+    _check(lib().sv_set_basis_state(sv, int(k)))
+
+
+def _host_dtype(sv: int):
+    n, d = sv_info(sv)
+    return n, (np.complex128 if d == SV_C128 else np.complex64)
+
+
+def sv_from_host(sv: int, amps: np.ndarray) -> None:
+    n, dt = _host_dtype(sv)
+    a = np.ascontiguousarray(amps, dtype=dt)
+    if a.shape != (1 << n,):
+        raise ValueError("amplitude array has the wrong length")
+    _check(lib().sv_from_host(sv, a.ctypes.data))
+
+
+def sv_to_host(sv: int, materialize_frame: bool = True, out: Optional[np.ndarray] = None) -> np.ndarray:
+    n, dt = _host_dtype(sv)
+    if out is None:
+        out = np.empty(1 << n, dtype=dt)
+    if out.dtype != dt or out.shape != (1 << n,) or not out.flags.c_contiguous:
+        raise ValueError("output array has the wrong dtype or shape")
+    _check(lib().sv_to_host(sv, out.ctypes.data, 1 if materialize_frame else 0))
+    return out
+
+
+def sv_materialize(sv: int) -> None:
+    _check(lib().sv_materialize(sv))
+
+
+def sv_copy(dst: int, src: int) -> None:
+    _check(lib().sv_copy(dst, src))
+
+
+def frame_reset(sv: int) -> None:
+    _check(lib().frame_reset(sv))
+
+
+def frame_apply_pauli(sv: int, pauli: str, qubit: int) -> None:
+    _check(lib().frame_apply_pauli(sv, pauli.encode()[:1], int(qubit)))
+
+
+def frame_get(sv: int) -> Tuple[int, int, int]:
+    x, z, q = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int()
+    _check(lib().frame_get(sv, ctypes.byref(x), ctypes.byref(z), ctypes.byref(q)))
+    return x.value, z.value, q.value
+
+
+def apply_pauli_rotations(sv: int, x, z, angles) -> None:
+    x, z, a = _u64(x), _u64(z), _f64(angles)
+    if not (len(x) == len(z) == len(a)):
+        raise ValueError("x, z and angles must have equal length")
+    _check(lib().apply_pauli_rotations(sv, _p(x), _p(z), _p(a), len(a)))
+
+
+def plan_create(n_qubits: int, dtype, x, z, angles, fusion_depth: int = -1, stream=None) -> int:
+    x, z, a = _u64(x), _u64(z), _f64(angles)
+    if not (len(x) == len(z) == len(a)):
+        raise ValueError("x, z and angles must have equal length")
+    h = ctypes.c_void_p()
+    _check(lib().plan_create(ctypes.byref(h), int(n_qubits), dtype_code(dtype), _p(x), _p(z), _p(a), len(a),
+                             int(fusion_depth), _stream(stream)))
+    return h.value
+
+
+def plan_apply(sv: int, plan: int) -> None:
+    _check(lib().plan_apply(sv, plan))
+
+
+def plan_free(plan: int) -> None:
+    _check(lib().plan_free(plan))
+
+
+def plan_stats(plan: int) -> Tuple[int, int, int]:
+    a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().plan_stats(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def trotter_expand(x, z, c, dt: float, steps: int, order: int = 1, merge: bool = False):
+    x, z, c = _u64(x), _u64(z), _f64(c)
+    cnt = ctypes.c_size_t()
+    L = lib()
+    _check(L.trotter_expand(_p(x), _p(z), _p(c), len(c), float(dt), int(steps), int(order), int(merge),
+                            None, None, None, 0, ctypes.byref(cnt)))
+    m = cnt.value
+    ox, oz, ot = np.empty(m, np.uint64), np.empty(m, np.uint64), np.empty(m, np.float64)
+    _check(L.trotter_expand(_p(x), _p(z), _p(c), len(c), float(dt), int(steps), int(order), int(merge),
+                            _p(ox), _p(oz), _p(ot), m, ctypes.byref(cnt)))
+    return ox, oz, ot
+
+
+def expval_pauli_sum(sv: int, x, z, coeff) -> Tuple[float, float]:
+    x, z, c = _u64(x), _u64(z), _f64(coeff)
+    e, nrm = ctypes.c_double(), ctypes.c_double()
+    _check(lib().expval_pauli_sum(sv, _p(x), _p(z), _p(c), len(c), ctypes.byref(e), ctypes.byref(nrm)))
+    return e.value, nrm.value
+
+
+def apply_pauli_sum(dst: int, src: int, x, z, coeff) -> None:
+    x, z, c = _u64(x), _u64(z), _f64(coeff)
+    _check(lib().apply_pauli_sum(dst, src, _p(x), _p(z), _p(c), len(c)))
+
+
+def rotation_grads(psi0: int, x, z, angles, hx, hz, hc) -> Tuple[float, np.ndarray]:
+    x, z, a = _u64(x), _u64(z), _f64(angles)
+    hx, hz, hc = _u64(hx), _u64(hz), _f64(hc)
+    g = np.empty(len(a), dtype=np.float64)
+    e = ctypes.c_double()
+    _check(lib().rotation_grads(psi0, _p(x), _p(z), _p(a), len(a), _p(hx), _p(hz), _p(hc), len(hc),
+                                ctypes.byref(e), _p(g)))
+    return e.value, g
+
+
+def apply_pauli_rotations_gates(sv: int, x, z, angles) -> int:
+    x, z, a = _u64(x), _u64(z), _f64(angles)
+    n = ctypes.c_size_t()
+    _check(lib().apply_pauli_rotations_gates(sv, _p(x), _p(z), _p(a), len(a), ctypes.byref(n)))
+    return n.value
+
+
+def batch_run(states: Sequence[int], plans: Sequence[int], use_graph: bool = True) -> None:
+    if len(states) != len(plans):
+        raise ValueError("states and plans must have equal length")
+    sa = (ctypes.c_void_p * len(states))(*states)
+    pa = (ctypes.c_void_p * len(plans))(*plans)
+    _check(lib().batch_run(sa, pa, len(states), 1 if use_graph else 0))
+
+
+class TraceRow(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+def sv_trace_start(sv: int) -> None:
+    _check(lib().sv_trace_start(sv))
+
+
+def sv_trace_stop(sv: int) -> dict:
+    """Returns {kernel name: (launches, total_ms, algorithmic_bytes)}."""
+    rows = (TraceRow * 64)()
+    n = ctypes.c_int()
+    _check(lib().sv_trace_stop(sv, rows, 64, ctypes.byref(n)))
+    return {rows[i].name.decode(): (int(rows[i].launches), float(rows[i].total_ms), float(rows[i].bytes))
+            for i in range(n.value)}

@@ -1,0 +1,477 @@
+// Host side of the rotation path: Trotter expansion, Pauli-frame rewrite,
+// angle reduction into the frame, and the planner that packs a rotation list
+// into fused runs (one HBM pass each).
+//
+// Tan form.  R_P(a) = cos(a/2) [I - i tan(a/2) P], so a pass can apply
+// a_k <- a_k - i t (P a)_k with one multiply-add per real component and leave
+// the positive factor cos(a/2) to a running scale that a later pass folds in.
+// With |a| <= pi/2 the factor is >= 1/sqrt2 and |t| <= 1.  Larger angles are
+// brought into range with R_P(a) = (-i P) R_P(a - pi) = (i P) R_P(a + pi): the
+// Pauli factor goes into the frame (paper: Pauli operations are absorbed by the
+// frame), so the device never sees it.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+
+#include "internal.h"
+
+namespace pr {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct Item {
+  uint64_t x, z;
+  double theta;   // as given
+  int64_t idx;    // position in the caller's list
+};
+
+// fold thresholds on log2 of the amplitude growth bound since the last fold
+double fold_half(int dtype) { return dtype == SV_C128 ? 400.0 : 30.0; }
+
+int default_depth(int dtype) { return dtype == SV_C128 ? 3 : 4; }
+
+uint64_t fixed_half_angle(double theta) {
+  // theta/2 as a fraction of a full turn in units of 2^-64 (wraps mod 2 pi)
+  double q = theta / (4.0 * kPi);
+  q -= std::nearbyint(q);  // [-0.5, 0.5]
+  double s = std::ldexp(q, 64);
+  if (s >= 9223372036854775807.0) return 0x8000000000000000ULL;
+  if (s <= -9223372036854775808.0) return 0x8000000000000000ULL;
+  return (uint64_t)(int64_t)std::llround(s);
+}
+
+struct RunBuilder {
+  uint64_t basis[kDMax];
+  int piv[kDMax];
+  int d = 0;
+  std::vector<size_t> members;  // indices into the effective list
+  double growth = 0.0;
+
+  void reset() {
+    d = 0;
+    members.clear();
+    growth = 0.0;
+  }
+  uint64_t reduce(uint64_t x) const {
+    for (int b = 0; b < d; ++b)
+      if ((x >> piv[b]) & 1ULL) x ^= basis[b];
+    return x;
+  }
+  void add_vector(uint64_t r) {
+    int p = 63 - __builtin_clzll(r);
+    for (int b = 0; b < d; ++b)
+      if ((basis[b] >> p) & 1ULL) basis[b] ^= r;
+    // insert keeping pivots ascending
+    int pos = d;
+    while (pos > 0 && piv[pos - 1] > p) {
+      basis[pos] = basis[pos - 1];
+      piv[pos] = piv[pos - 1];
+      --pos;
+    }
+    basis[pos] = r;
+    piv[pos] = p;
+    ++d;
+  }
+};
+
+struct Eff {
+  uint64_t x, z;
+  double t;      // tan of the reduced angle (plan-frame sign included)
+  double c;      // cos of the reduced angle
+};
+
+}  // namespace
+
+int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *z,
+               const double *theta, size_t count, int fusion_depth, cudaStream_t stream) {
+  (void)stream;
+  if (n < 1 || n > max_qubits(dtype)) return fail(SV_EINVAL, "bad n_qubits %d", n);
+  if (count && (!x || !z || !theta)) return fail(SV_EINVAL, "NULL rotation arrays");
+  int rc = validate_masks(n, x, z, count);
+  if (rc) return rc;
+  for (size_t j = 0; j < count; ++j)
+    if (!std::isfinite(theta[j])) return fail(SV_EINVAL, "angle %zu is not finite", j);
+  int dmax = fusion_depth < 0 ? default_depth(dtype) : fusion_depth;
+  if (dmax > kDMax) return fail(SV_EINVAL, "fusion_depth must be <= %d", kDMax);
+  if (dmax > n) dmax = n;
+
+  p->n = n;
+  p->dtype = dtype;
+  p->dmax = dmax;
+  p->runs.clear();
+  p->n_input = count;
+  p->frame = Pauli();
+  p->order.clear();
+  p->beta.clear();
+  p->sigma.clear();
+  p->ox.clear();
+  p->oz.clear();
+
+  std::vector<RotDev> rots;
+  std::vector<DiagDev> diags;
+  std::complex<double> scale(1.0, 0.0);
+  double growth_since_fold = 0.0;
+
+  // identity strings: a global phase, kept in the scale
+  std::vector<Item> items;
+  items.reserve(count);
+  for (size_t j = 0; j < count; ++j) {
+    if (x[j] == 0 && z[j] == 0) {
+      scale *= std::exp(std::complex<double>(0.0, -0.5 * theta[j]));
+      p->order.push_back((int64_t)j);
+      p->beta.push_back(0.0);
+      p->sigma.push_back(0);  // marks an identity (zero gradient)
+      p->ox.push_back(0);
+      p->oz.push_back(0);
+      continue;
+    }
+    items.push_back({x[j], z[j], theta[j], (int64_t)j});
+  }
+
+  // diagonal stretches long enough for the phase-sum pass
+  const size_t diag_min = 8;
+  std::vector<int> in_diag(items.size(), 0);
+  if (n >= kDiagMinQubits) {
+    size_t a = 0;
+    while (a < items.size()) {
+      if (items[a].x != 0) {
+        ++a;
+        continue;
+      }
+      size_t b = a;
+      while (b < items.size() && items[b].x == 0) ++b;
+      if (b - a >= diag_min)
+        for (size_t k = a; k < b; ++k) in_diag[k] = 1;
+      a = b;
+    }
+  }
+
+  RunBuilder rb;
+  std::vector<Eff> eff;
+  eff.reserve(items.size());
+  Pauli qp;  // frame factors taken out so far (plan frame)
+  const double gcap = fold_half(dtype);
+
+  auto finish_coset_run = [&](bool force_fold) {
+    if (rb.members.empty() && !force_fold) return;
+    RunDev r;
+    std::memset(&r, 0, sizeof(r));
+    r.kind = 0;
+    r.d = rb.d;
+    for (int b = 0; b < rb.d; ++b) {
+      r.basis[b] = rb.basis[b];
+      r.piv[b] = rb.piv[b];
+    }
+    r.first = (int32_t)rots.size();
+    r.count = (int32_t)rb.members.size();
+    for (size_t m : rb.members) {
+      const Eff &e = eff[m];
+      uint32_t u = 0;
+      for (int b = 0; b < rb.d; ++b)
+        if ((e.x >> rb.piv[b]) & 1ULL) u |= 1u << b;
+      uint32_t zt = 0;
+      for (int l = 0; l < (1 << rb.d); ++l) {
+        uint64_t s = 0;
+        for (int b = 0; b < rb.d; ++b)
+          if ((l >> b) & 1) s ^= rb.basis[b];
+        zt |= (uint32_t)(popc64(s & e.z) & 1) << l;
+      }
+      int ny = popc64(e.x & e.z) & 3;
+      int imag = (ny & 1) == 0;
+      double ks = (ny == 0 || ny == 1) ? -1.0 : 1.0;  // kappa = (-i)^{nY+1}
+      RotDev d;
+      d.x = e.x;
+      d.z = e.z;
+      d.t = ks * e.t;
+      d.zt = zt;
+      d.code = (u << 1) | (uint32_t)imag;
+      rots.push_back(d);
+    }
+    growth_since_fold += rb.growth;
+    if (force_fold || growth_since_fold > gcap) {
+      r.fold = 1;
+      r.fold_re = scale.real();
+      r.fold_im = scale.imag();
+      scale = std::complex<double>(1.0, 0.0);
+      growth_since_fold = 0.0;
+    }
+    p->runs.push_back(r);
+    rb.reset();
+  };
+
+  size_t k = 0;
+  while (k < items.size()) {
+    if (in_diag[k]) {
+      finish_coset_run(false);
+      size_t b = k;
+      while (b < items.size() && in_diag[b] && b - k < (size_t)kMaxDiagRots) ++b;
+      // one phase-sum run over items[k, b); all diagonal, so any order is exact
+      std::vector<DiagDev> chunk;
+      std::vector<int> cls;
+      for (size_t m = k; m < b; ++m) {
+        const Item &it = items[m];
+        int sp = anticommute(it.x, it.z, qp.x, qp.z) ? -1 : 1;
+        DiagDev dd;
+        dd.z = it.z;
+        dd.a = fixed_half_angle(sp * it.theta);
+        chunk.push_back(dd);
+        cls.push_back((int)((it.z >> kDiagClassLo) & ((1u << kDiagClassBits) - 1)));
+        p->order.push_back(it.idx);
+        p->beta.push_back(sp * it.theta);
+        p->sigma.push_back((int8_t)sp);
+        p->ox.push_back(it.x);
+        p->oz.push_back(it.z);
+      }
+      // stable sort by class; the adjoint order follows the device order
+      std::vector<size_t> perm(chunk.size());
+      for (size_t m = 0; m < perm.size(); ++m) perm[m] = m;
+      std::stable_sort(perm.begin(), perm.end(), [&](size_t a1, size_t b1) { return cls[a1] < cls[b1]; });
+      size_t base_order = p->order.size() - chunk.size();
+      std::vector<int64_t> o2(chunk.size());
+      std::vector<double> b2(chunk.size());
+      std::vector<int8_t> s2(chunk.size());
+      std::vector<uint64_t> x2(chunk.size()), z2(chunk.size());
+      RunDev r;
+      std::memset(&r, 0, sizeof(r));
+      r.kind = 1;
+      r.first = (int32_t)diags.size();
+      r.count = (int32_t)chunk.size();
+      int cur = 0;
+      r.seg[0] = 0;
+      for (size_t m = 0; m < perm.size(); ++m) {
+        size_t src = perm[m];
+        while (cur < cls[src]) r.seg[++cur] = (int32_t)m;
+        diags.push_back(chunk[src]);
+        o2[m] = p->order[base_order + src];
+        b2[m] = p->beta[base_order + src];
+        s2[m] = p->sigma[base_order + src];
+        x2[m] = p->ox[base_order + src];
+        z2[m] = p->oz[base_order + src];
+      }
+      while (cur < (1 << kDiagClassBits)) r.seg[++cur] = (int32_t)perm.size();
+      for (size_t m = 0; m < perm.size(); ++m) {
+        p->order[base_order + m] = o2[m];
+        p->beta[base_order + m] = b2[m];
+        p->sigma[base_order + m] = s2[m];
+        p->ox[base_order + m] = x2[m];
+        p->oz[base_order + m] = z2[m];
+      }
+      p->runs.push_back(r);
+      p->n_diag_runs++;
+      k = b;
+      continue;
+    }
+
+    const Item &it = items[k];
+    int sp = anticommute(it.x, it.z, qp.x, qp.z) ? -1 : 1;
+    double a = sp * it.theta;
+    // exp(-i a/2 P) is periodic up to sign: a -> a - 2 pi m gives a factor (-1)^m
+    double m2 = std::nearbyint(a / (2.0 * kPi));
+    if (m2 != 0.0) {
+      a -= 2.0 * kPi * m2;
+      if (std::fmod(std::fabs(m2), 2.0) == 1.0) scale = -scale;
+    }
+    if (a > 0.5 * kPi) {
+      // R_P(a) = (-i P) R_P(a - pi)
+      a -= kPi;
+      Pauli f = pauli_string(it.x, it.z);
+      f.q = (f.q + 3) & 3;
+      qp = pauli_mul(qp, f);
+    } else if (a < -0.5 * kPi) {
+      // R_P(a) = (i P) R_P(a + pi)
+      a += kPi;
+      Pauli f = pauli_string(it.x, it.z);
+      f.q = (f.q + 1) & 3;
+      qp = pauli_mul(qp, f);
+    }
+    Eff e;
+    e.x = it.x;
+    e.z = it.z;
+    e.t = std::tan(0.5 * a);
+    e.c = std::cos(0.5 * a);
+    double g = -std::log2(e.c);
+    p->order.push_back(it.idx);
+    p->beta.push_back(a);
+    p->sigma.push_back((int8_t)sp);
+    p->ox.push_back(it.x);
+    p->oz.push_back(it.z);
+
+    // does it fit the open run?
+    bool fits = rb.members.size() < (size_t)kMaxRunRots && rb.growth + g <= gcap;
+    uint64_t r = 0;
+    if (fits && it.x != 0) {
+      r = rb.reduce(it.x);
+      if (r != 0 && rb.d >= dmax) fits = false;
+    }
+    if (!fits) {
+      finish_coset_run(false);
+      r = it.x ? rb.reduce(it.x) : 0;
+    }
+    if (r != 0) rb.add_vector(r);
+    eff.push_back(e);
+    rb.members.push_back(eff.size() - 1);
+    rb.growth += g;
+    scale *= e.c;
+    ++k;
+  }
+  bool need_fold = std::abs(scale - std::complex<double>(1.0, 0.0)) != 0.0;
+  if (!rb.members.empty()) {
+    finish_coset_run(need_fold);
+  } else if (need_fold) {
+    if (!p->runs.empty()) {
+      RunDev &last = p->runs.back();
+      // multiply onto an existing fold or add one
+      std::complex<double> f = last.fold ? std::complex<double>(last.fold_re, last.fold_im) : 1.0;
+      f *= scale;
+      last.fold = 1;
+      last.fold_re = f.real();
+      last.fold_im = f.imag();
+    } else {
+      finish_coset_run(true);  // an empty d = 0 run that only scales
+    }
+  }
+  p->frame = qp;
+  p->n_effective = items.size();
+  p->n_rots = rots.size();
+  p->n_diag = diags.size();
+
+  if (!diags.empty()) {
+    rc = prepare_tables(dtype);
+    if (rc) return rc;
+  }
+  // upload
+  if (p->d_rots) cudaFree(p->d_rots);
+  if (p->d_diag) cudaFree(p->d_diag);
+  p->d_rots = nullptr;
+  p->d_diag = nullptr;
+  if (!rots.empty()) {
+    if (cudaMalloc(&p->d_rots, rots.size() * sizeof(RotDev)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SV_ENOMEM, "plan upload allocation failed");
+    }
+    PR_CUDA(cudaMemcpy(p->d_rots, rots.data(), rots.size() * sizeof(RotDev), cudaMemcpyHostToDevice));
+  }
+  if (!diags.empty()) {
+    if (cudaMalloc(&p->d_diag, diags.size() * sizeof(DiagDev)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SV_ENOMEM, "plan upload allocation failed");
+    }
+    PR_CUDA(cudaMemcpy(p->d_diag, diags.data(), diags.size() * sizeof(DiagDev), cudaMemcpyHostToDevice));
+  }
+  return SV_OK;
+}
+
+int apply_plan(sv_state *sv, sv_plan *plan) {
+  if (!sv || !plan) return fail(SV_EINVAL, "NULL argument");
+  if (sv->n != plan->n || sv->dtype != plan->dtype)
+    return fail(SV_EINVAL, "plan built for n=%d dtype=%d, state has n=%d dtype=%d", plan->n, plan->dtype,
+                sv->n, sv->dtype);
+  const Pauli q0 = sv->frame;
+  for (const RunDev &r : plan->runs) {
+    int rc = launch_run(sv, plan, r, q0.x, q0.z);
+    if (rc) return rc;
+  }
+  // Q <- Q0 Qp (-1)^{<Qp, Q0>}: the frame factors picked up the runtime signs
+  Pauli f = pauli_mul(q0, plan->frame);
+  if (anticommute(plan->frame.x, plan->frame.z, q0.x, q0.z)) f.q = (f.q + 2) & 3;
+  sv->frame = f;
+  return SV_OK;
+}
+
+}  // namespace pr
+
+using namespace pr;
+
+extern "C" {
+
+int plan_create(sv_plan **out, int n_qubits, int dtype, const uint64_t *x, const uint64_t *z,
+                const double *angles, size_t count, int fusion_depth, void *cuda_stream) {
+  if (!out) return fail(SV_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (dtype != SV_C128 && dtype != SV_C64) return fail(SV_EINVAL, "bad dtype");
+  sv_plan *p = new (std::nothrow) sv_plan();
+  if (!p) return fail(SV_ENOMEM, "host allocation failed");
+  int rc = build_plan(p, n_qubits, dtype, x, z, angles, count, fusion_depth, (cudaStream_t)cuda_stream);
+  if (rc) {
+    plan_free(p);
+    return rc;
+  }
+  *out = p;
+  return SV_OK;
+}
+
+int plan_apply(sv_state *sv, sv_plan *plan) { return apply_plan(sv, plan); }
+
+int plan_free(sv_plan *plan) {
+  if (!plan) return SV_OK;
+  cudaDeviceSynchronize();
+  if (plan->d_rots) cudaFree(plan->d_rots);
+  if (plan->d_diag) cudaFree(plan->d_diag);
+  delete plan;
+  return SV_OK;
+}
+
+int plan_stats(const sv_plan *plan, size_t *n_rotations, size_t *n_runs, size_t *n_diag_runs) {
+  if (!plan) return fail(SV_EINVAL, "plan is NULL");
+  if (n_rotations) *n_rotations = plan->n_effective;
+  if (n_runs) *n_runs = plan->runs.size();
+  if (n_diag_runs) *n_diag_runs = plan->n_diag_runs;
+  return SV_OK;
+}
+
+int apply_pauli_rotations(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *angles,
+                          size_t count) {
+  if (!sv) return fail(SV_EINVAL, "sv is NULL");
+  sv_plan *p = nullptr;
+  int rc = plan_create(&p, sv->n, sv->dtype, x, z, angles, count, -1, sv->stream);
+  if (rc) return rc;
+  rc = apply_plan(sv, p);
+  plan_free(p);
+  return rc;
+}
+
+int trotter_expand(const uint64_t *x, const uint64_t *z, const double *c, size_t n_terms, double dt,
+                   int steps, int order, int merge, uint64_t *out_x, uint64_t *out_z, double *out_theta,
+                   size_t cap, size_t *out_count) {
+  if (!out_count) return fail(SV_EINVAL, "out_count is NULL");
+  if (n_terms && (!x || !z || !c)) return fail(SV_EINVAL, "NULL term arrays");
+  if (order != 1 && order != 2) return fail(SV_EINVAL, "order must be 1 or 2");
+  if (steps < 0) return fail(SV_EINVAL, "steps must be >= 0");
+  if (cap && (!out_x || !out_z || !out_theta)) return fail(SV_EINVAL, "NULL output arrays");
+  if (!std::isfinite(dt)) return fail(SV_EINVAL, "dt is not finite");
+  size_t w = 0;
+  // merging needs the previous entry; when cap is too small count exactly
+  // with a shadow of the last emitted string
+  uint64_t last_x = ~0ULL, last_z = ~0ULL;
+  bool have_last = false;
+  auto emit2 = [&](uint64_t xx, uint64_t zz, double th) {
+    if (merge && have_last && last_x == xx && last_z == zz) {
+      if (w - 1 < cap) out_theta[w - 1] += th;
+      return;
+    }
+    if (w < cap) {
+      out_x[w] = xx;
+      out_z[w] = zz;
+      out_theta[w] = th;
+    }
+    ++w;
+    last_x = xx;
+    last_z = zz;
+    have_last = true;
+  };
+  for (int s = 0; s < steps; ++s) {
+    if (order == 1) {
+      for (size_t j = 0; j < n_terms; ++j) emit2(x[j], z[j], 2.0 * c[j] * dt);
+    } else {
+      for (size_t j = 0; j < n_terms; ++j) emit2(x[j], z[j], c[j] * dt);
+      for (size_t j = n_terms; j-- > 0;) emit2(x[j], z[j], c[j] * dt);
+    }
+  }
+  *out_count = w;
+  return SV_OK;
+}
+
+}  // extern "C"

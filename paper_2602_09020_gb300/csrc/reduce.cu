@@ -1,0 +1,685 @@
+// FP64 reductions over the statevector.
+//
+// <psi|sum_j c_j P_j|psi> (paper, Sec. "Extraction of Expectation Values",
+// Eq. chfsexp) with |psi> = Q|phi>: every term is first rewritten by the Pauli
+// frame (Q^dag P Q = (-1)^{<P,Q>} P, Eq. Fmap for a Pauli-only frame), then
+// terms are grouped by x-mask.  For a group with x != 0 each pair (k, k^x)
+// contributes
+//     sum_j c_j i^{nY_j} [ s_j(k^x) w + s_j(k) conj(w) ],  w = conj(a_k) a_{k^x},
+// which is 2 c_j s_j(k) times Re w, Im w, -Re w or -Im w for nY = 0, 1, 2, 3
+// (mod 4), s_j(k) = (-1)^{popc(k & z_j)}.  The x = 0 group contributes
+// sum_k |a_k|^2 sum_j c_j s_j(k).  Groups whose x-masks span a subspace of
+// dimension <= kExpD are evaluated in one read pass over cosets of that span,
+// as in the fused rotation pass.  Amplitudes are widened to FP64 before any
+// product; every sum is FP64; block partials are reduced in a fixed order, so
+// results are bitwise reproducible.
+#include <algorithm>
+#include <cstring>
+#include <map>
+
+#include "internal.h"
+
+namespace pr {
+
+namespace {
+
+constexpr int kExpD = 4;
+constexpr int kExpMaxTerms = 1024;
+constexpr int kExpMaxGroups = 1 << kExpD;
+
+template <typename R>
+struct Cx;
+template <>
+struct Cx<float> {
+  using T = float2;
+};
+template <>
+struct Cx<double> {
+  using T = double2;
+};
+
+__device__ __forceinline__ int parity(uint32_t v) { return __popc(v) & 1; }
+__device__ __forceinline__ int parity(uint64_t v) { return __popcll(v) & 1; }
+
+struct ExpTermSm {
+  uint64_t z;
+  double coef;
+  uint32_t zt;
+  uint32_t imag;
+};
+
+template <int D, int U, typename Idx>
+__device__ __forceinline__ void group_terms(const double2 (&a)[1 << D], Idx rep, const ExpTermSm *terms,
+                                            int first, int count, double &acc) {
+  constexpr int E = 1 << D;
+  if (U == 0) {
+    double p[E];
+#pragma unroll
+    for (int l = 0; l < E; ++l) p[l] = a[l].x * a[l].x + a[l].y * a[l].y;
+    for (int j = first; j < first + count; ++j) {
+      const ExpTermSm t = terms[j];
+      const uint32_t s0 = (uint32_t)parity((uint64_t)rep & t.z);
+#pragma unroll
+      for (int l = 0; l < E; ++l) {
+        const double c = ((s0 ^ (t.zt >> l)) & 1u) ? -t.coef : t.coef;
+        acc = fma(c, p[l], acc);
+      }
+    }
+  } else {
+    double wr[E], wi[E];
+#pragma unroll
+    for (int l = 0; l < E; ++l) {
+      if ((l ^ U) > l) {
+        const double2 al = a[l], am = a[l ^ U];
+        wr[l] = al.x * am.x + al.y * am.y;
+        wi[l] = al.x * am.y - al.y * am.x;
+      } else {
+        wr[l] = 0.0;
+        wi[l] = 0.0;
+      }
+    }
+    for (int j = first; j < first + count; ++j) {
+      const ExpTermSm t = terms[j];
+      const uint32_t s0 = (uint32_t)parity((uint64_t)rep & t.z);
+      if (t.imag) {
+#pragma unroll
+        for (int l = 0; l < E; ++l)
+          if ((l ^ U) > l) {
+            const double c = ((s0 ^ (t.zt >> l)) & 1u) ? -t.coef : t.coef;
+            acc = fma(c, wi[l], acc);
+          }
+      } else {
+#pragma unroll
+        for (int l = 0; l < E; ++l)
+          if ((l ^ U) > l) {
+            const double c = ((s0 ^ (t.zt >> l)) & 1u) ? -t.coef : t.coef;
+            acc = fma(c, wr[l], acc);
+          }
+      }
+    }
+  }
+}
+
+#define PR_GCASE(K) \
+  case K:           \
+    if constexpr ((K) < (1 << D)) group_terms<D, (K)>(a, rep, terms, first, count, acc); \
+    break;
+
+template <int D, typename Idx>
+__device__ __forceinline__ void group_dispatch(int u, const double2 (&a)[1 << D], Idx rep, const ExpTermSm *terms,
+                                               int first, int count, double &acc) {
+  switch (u) {
+    PR_GCASE(0) PR_GCASE(1) PR_GCASE(2) PR_GCASE(3) PR_GCASE(4) PR_GCASE(5) PR_GCASE(6) PR_GCASE(7)
+    PR_GCASE(8) PR_GCASE(9) PR_GCASE(10) PR_GCASE(11) PR_GCASE(12) PR_GCASE(13) PR_GCASE(14) PR_GCASE(15)
+    default: break;
+  }
+}
+
+// block sum of two doubles in a fixed order; thread 0 gets the result
+__device__ __forceinline__ void block_sum2(double &a, double &b) {
+  __shared__ double sa[kThreads / 32], sb[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ra = 0.0, rb = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      ra += sa[i];
+      rb += sb[i];
+    }
+    a = ra;
+    b = rb;
+  }
+}
+
+template <typename R, typename Idx, int D>
+__global__ void __launch_bounds__(kThreads)
+    k_expval(const typename Cx<R>::T *__restrict__ amp, Idx n_cosets, const ExpRunDev run,
+             const ExpGroupDev *__restrict__ groups, const ExpTermDev *__restrict__ gterms,
+             double *__restrict__ partials) {
+  constexpr int E = 1 << D;
+  __shared__ ExpTermSm terms[kExpMaxTerms];
+  __shared__ ExpGroupDev sg[kExpMaxGroups];
+  __shared__ Idx soff[E];
+  int n_terms = 0;
+  for (int g = 0; g < run.n_groups; ++g) n_terms = max(n_terms, groups[g].first + groups[g].count);
+  for (int j = threadIdx.x; j < n_terms; j += blockDim.x) {
+    const ExpTermDev t = gterms[j];
+    terms[j] = ExpTermSm{t.z, t.coef, t.zt, t.imag};
+  }
+  if (threadIdx.x < run.n_groups) sg[threadIdx.x] = groups[threadIdx.x];
+  if (threadIdx.x < E) {
+    uint64_t s = 0;
+    for (int b = 0; b < D; ++b)
+      if ((threadIdx.x >> b) & 1) s ^= run.basis[b];
+    soff[threadIdx.x] = (Idx)s;
+  }
+  __syncthreads();
+  double acc = 0.0, nrm = 0.0;
+  const Idx stride = (Idx)gridDim.x * blockDim.x;
+  for (Idx c = (Idx)blockIdx.x * blockDim.x + threadIdx.x; c < n_cosets; c += stride) {
+    Idx rep = c;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const int p = run.piv[b];
+      rep = ((rep >> p) << (p + 1)) | (rep & ((Idx(1) << p) - 1));
+    }
+    double2 a[E];
+#pragma unroll
+    for (int l = 0; l < E; ++l) {
+      const typename Cx<R>::T v = amp[rep ^ soff[l]];
+      a[l].x = (double)v.x;
+      a[l].y = (double)v.y;
+    }
+    if (run.with_norm) {
+#pragma unroll
+      for (int l = 0; l < E; ++l) nrm = fma(a[l].x, a[l].x, fma(a[l].y, a[l].y, nrm));
+    }
+    for (int g = 0; g < run.n_groups; ++g) {
+      const ExpGroupDev G = sg[g];
+      group_dispatch<D>(G.u, a, rep, terms, G.first, G.count, acc);
+    }
+  }
+  block_sum2(acc, nrm);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = acc;
+    partials[2 * blockIdx.x + 1] = nrm;
+  }
+}
+
+// result[2 r + i] = sum over blocks of partials[r][b][i], fixed order
+__global__ void k_finish(const double *__restrict__ partials, int n_blocks, double *__restrict__ result) {
+  const double *p = partials + (size_t)blockIdx.x * 2 * n_blocks;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) {
+    a += p[2 * i];
+    b += p[2 * i + 1];
+  }
+  block_sum2(a, b);
+  if (threadIdx.x == 0) {
+    result[2 * blockIdx.x] = a;
+    result[2 * blockIdx.x + 1] = b;
+  }
+}
+
+// dst += sum_g sum_{j in g} c_j i^{nY_j} s_j(k^x) src_{k^x}   (per element k)
+template <typename R, typename Idx, int D>
+__global__ void __launch_bounds__(kThreads)
+    k_pauli_sum(typename Cx<R>::T *__restrict__ dst, const typename Cx<R>::T *__restrict__ src, Idx n_cosets,
+                const ExpRunDev run, const ExpGroupDev *__restrict__ groups,
+                const ExpTermDev *__restrict__ gterms) {
+  using C = typename Cx<R>::T;
+  constexpr int E = 1 << D;
+  __shared__ ExpTermSm terms[kExpMaxTerms];
+  __shared__ ExpGroupDev sg[kExpMaxGroups];
+  __shared__ Idx soff[E];
+  int n_terms = 0;
+  for (int g = 0; g < run.n_groups; ++g) n_terms = max(n_terms, groups[g].first + groups[g].count);
+  for (int j = threadIdx.x; j < n_terms; j += blockDim.x) {
+    const ExpTermDev t = gterms[j];
+    terms[j] = ExpTermSm{t.z, t.coef, t.zt, t.imag};
+  }
+  if (threadIdx.x < run.n_groups) sg[threadIdx.x] = groups[threadIdx.x];
+  if (threadIdx.x < E) {
+    uint64_t s = 0;
+    for (int b = 0; b < D; ++b)
+      if ((threadIdx.x >> b) & 1) s ^= run.basis[b];
+    soff[threadIdx.x] = (Idx)s;
+  }
+  __syncthreads();
+  const Idx stride = (Idx)gridDim.x * blockDim.x;
+  for (Idx c = (Idx)blockIdx.x * blockDim.x + threadIdx.x; c < n_cosets; c += stride) {
+    Idx rep = c;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const int p = run.piv[b];
+      rep = ((rep >> p) << (p + 1)) | (rep & ((Idx(1) << p) - 1));
+    }
+    double2 a[E], o[E];
+#pragma unroll
+    for (int l = 0; l < E; ++l) {
+      const C v = src[rep ^ soff[l]];
+      a[l].x = (double)v.x;
+      a[l].y = (double)v.y;
+      const C w = dst[rep ^ soff[l]];
+      o[l].x = (double)w.x;
+      o[l].y = (double)w.y;
+    }
+    for (int g = 0; g < run.n_groups; ++g) {
+      const ExpGroupDev G = sg[g];
+      const int u = G.u;
+#pragma unroll
+      for (int l = 0; l < E; ++l) {
+        const int m = l ^ u;
+        double cr = 0.0, ci = 0.0;  // sum_j c_j i^{nY} s_j(k_m)
+        for (int j = G.first; j < G.first + G.count; ++j) {
+          const ExpTermSm t = terms[j];
+          const uint32_t s = (uint32_t)parity((uint64_t)rep & t.z) ^ ((t.zt >> m) & 1u);
+          const double cc = (s & 1u) ? -t.coef : t.coef;
+          switch (t.imag & 3u) {
+            case 0: cr += cc; break;
+            case 1: ci += cc; break;
+            case 2: cr -= cc; break;
+            default: ci -= cc; break;
+          }
+        }
+        // a[m] read with a runtime index: keep the select explicit
+        double2 am = a[0];
+#pragma unroll
+        for (int q = 1; q < E; ++q)
+          if (q == m) am = a[q];
+        o[l].x = fma(cr, am.x, fma(-ci, am.y, o[l].x));
+        o[l].y = fma(cr, am.y, fma(ci, am.x, o[l].y));
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < E; ++l) {
+      C w;
+      w.x = (R)o[l].x;
+      w.y = (R)o[l].y;
+      dst[rep ^ soff[l]] = w;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host planning
+
+struct HostExpRun {
+  ExpRunDev dev;
+  std::vector<ExpGroupDev> groups;
+  std::vector<ExpTermDev> terms;
+};
+
+struct Term {
+  uint64_t x, z;
+  double c;
+};
+
+// group terms by x (frame signs applied), then pack groups greedily into runs
+// whose x-masks span at most kExpD dimensions.  mode 0: expectation
+// coefficients (2 c s(nY) per pair, c per element on x = 0; imag = nY odd);
+// mode 1: Pauli-sum application (c with imag = nY mod 4).
+void plan_groups(const sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c, size_t count,
+                 int mode, std::vector<HostExpRun> &runs) {
+  const Pauli &q = sv->frame;
+  std::map<uint64_t, std::vector<Term>> by_x;
+  for (size_t j = 0; j < count; ++j) {
+    double cj = c[j];
+    if (anticommute(x[j], z[j], q.x, q.z)) cj = -cj;
+    by_x[x[j]].push_back({x[j], z[j], cj});
+  }
+  // split oversized groups
+  std::vector<std::vector<Term>> groups;
+  for (auto &kv : by_x) {
+    auto &v = kv.second;
+    for (size_t a = 0; a < v.size(); a += kExpMaxTerms)
+      groups.emplace_back(v.begin() + a, v.begin() + std::min(v.size(), a + (size_t)kExpMaxTerms));
+  }
+  std::vector<char> used(groups.size(), 0);
+  size_t left = groups.size();
+  const int dmax = std::min(kExpD, sv->n);
+  while (left > 0 || runs.empty()) {
+    HostExpRun r;
+    std::memset(&r.dev, 0, sizeof(r.dev));
+    uint64_t basis[kDMax];
+    int piv[kDMax];
+    int d = 0;
+    auto reduce = [&](uint64_t v) {
+      for (int b = 0; b < d; ++b)
+        if ((v >> piv[b]) & 1ULL) v ^= basis[b];
+      return v;
+    };
+    std::vector<size_t> members;
+    size_t n_terms = 0;
+    for (size_t g = 0; g < groups.size(); ++g) {
+      if (used[g]) continue;
+      if ((int)members.size() >= kExpMaxGroups) break;
+      if (n_terms + groups[g].size() > (size_t)kExpMaxTerms) continue;
+      uint64_t rr = reduce(groups[g][0].x);
+      if (rr != 0) {
+        if (d >= dmax) continue;
+        int p = 63 - __builtin_clzll(rr);
+        for (int b = 0; b < d; ++b)
+          if ((basis[b] >> p) & 1ULL) basis[b] ^= rr;
+        int pos = d;
+        while (pos > 0 && piv[pos - 1] > p) {
+          basis[pos] = basis[pos - 1];
+          piv[pos] = piv[pos - 1];
+          --pos;
+        }
+        basis[pos] = rr;
+        piv[pos] = p;
+        ++d;
+      }
+      used[g] = 1;
+      --left;
+      members.push_back(g);
+      n_terms += groups[g].size();
+    }
+    r.dev.d = d;
+    for (int b = 0; b < d; ++b) {
+      r.dev.basis[b] = basis[b];
+      r.dev.piv[b] = piv[b];
+    }
+    for (size_t g : members) {
+      ExpGroupDev G;
+      G.u = 0;
+      for (int b = 0; b < d; ++b)
+        if ((groups[g][0].x >> piv[b]) & 1ULL) G.u |= 1 << b;
+      G.first = (int32_t)r.terms.size();
+      G.count = (int32_t)groups[g].size();
+      G.pad = 0;
+      for (const Term &t : groups[g]) {
+        ExpTermDev e;
+        e.z = t.z;
+        uint32_t zt = 0;
+        for (int l = 0; l < (1 << d); ++l) {
+          uint64_t s = 0;
+          for (int b = 0; b < d; ++b)
+            if ((l >> b) & 1) s ^= basis[b];
+          zt |= (uint32_t)(popc64(s & t.z) & 1) << l;
+        }
+        e.zt = zt;
+        int ny = popc64(t.x & t.z) & 3;
+        if (mode == 0) {
+          if (t.x == 0) {
+            e.coef = t.c;
+            e.imag = 0;
+          } else {
+            e.coef = 2.0 * t.c * ((ny == 0 || ny == 1) ? 1.0 : -1.0);
+            e.imag = ny & 1;
+          }
+        } else {
+          e.coef = t.c;
+          e.imag = (uint32_t)ny;
+        }
+        r.terms.push_back(e);
+      }
+      r.groups.push_back(G);
+    }
+    r.dev.n_groups = (int32_t)r.groups.size();
+    r.dev.with_norm = runs.empty() ? 1 : 0;
+    runs.push_back(std::move(r));
+    if (left == 0) break;
+  }
+}
+
+// stage all runs' groups and terms in one copy; returns device pointers per run
+int stage_runs(sv_state *sv, const std::vector<HostExpRun> &runs, std::vector<const ExpGroupDev *> &dg,
+               std::vector<const ExpTermDev *> &dt) {
+  size_t bytes = 0;
+  std::vector<size_t> og(runs.size()), ot(runs.size());
+  for (size_t r = 0; r < runs.size(); ++r) {
+    og[r] = bytes;
+    bytes += (runs[r].groups.size() * sizeof(ExpGroupDev) + 15) & ~size_t(15);
+    ot[r] = bytes;
+    bytes += (runs[r].terms.size() * sizeof(ExpTermDev) + 15) & ~size_t(15);
+  }
+  if (bytes == 0) bytes = 16;
+  // the previous call's copy out of the pinned stage must be complete
+  PR_CUDA(cudaStreamSynchronize(sv->stream));
+  int rc = ensure_stage(sv, bytes);
+  if (rc) return rc;
+  char *h = (char *)sv->h_stage;
+  for (size_t r = 0; r < runs.size(); ++r) {
+    if (!runs[r].groups.empty())
+      std::memcpy(h + og[r], runs[r].groups.data(), runs[r].groups.size() * sizeof(ExpGroupDev));
+    if (!runs[r].terms.empty())
+      std::memcpy(h + ot[r], runs[r].terms.data(), runs[r].terms.size() * sizeof(ExpTermDev));
+  }
+  PR_CUDA(cudaMemcpyAsync(sv->d_stage, h, bytes, cudaMemcpyHostToDevice, sv->stream));
+  dg.resize(runs.size());
+  dt.resize(runs.size());
+  for (size_t r = 0; r < runs.size(); ++r) {
+    dg[r] = (const ExpGroupDev *)((char *)sv->d_stage + og[r]);
+    dt[r] = (const ExpTermDev *)((char *)sv->d_stage + ot[r]);
+  }
+  return SV_OK;
+}
+
+template <typename K>
+int occ_blocks(K kernel) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return (per_sm > 0 ? per_sm : 1) * device_sm_count();
+}
+
+template <typename R, typename Idx, int D>
+int run_expval_t(sv_state *sv, const std::vector<HostExpRun> &runs, const std::vector<const ExpGroupDev *> &dg,
+                 const std::vector<const ExpTermDev *> &dt, double *energy, double *norm2) {
+  using C = typename Cx<R>::T;
+  static int cap = 0;
+  if (!cap) cap = occ_blocks(k_expval<R, Idx, D>);
+  const uint64_t n_cosets = (1ULL << sv->n) >> D;
+  uint64_t need = (n_cosets + kThreads - 1) / kThreads;
+  int blocks = (int)(need < (uint64_t)cap ? need : (uint64_t)cap);
+  if (blocks < 1) blocks = 1;
+  int rc = ensure_scratch(sv, (size_t)2 * blocks * runs.size(), 2 * runs.size());
+  if (rc) return rc;
+  for (size_t r = 0; r < runs.size(); ++r) {
+    const int tr = trace_begin(sv);
+    k_expval<R, Idx, D><<<blocks, kThreads, 0, sv->stream>>>((const C *)sv->amps, (Idx)n_cosets, runs[r].dev,
+                                                            dg[r], dt[r], sv->d_partials + 2 * blocks * r);
+    PR_CHECK_LAUNCH();
+    trace_end(sv, tr, KN_EXPVAL, (double)sizeof(C) * (double)(1ULL << sv->n));
+  }
+  const int tr = trace_begin(sv);
+  k_finish<<<(unsigned)runs.size(), kThreads, 0, sv->stream>>>(sv->d_partials, blocks, sv->d_results);
+  PR_CHECK_LAUNCH();
+  trace_end(sv, tr, KN_FINISH, 16.0 * blocks * runs.size());
+  PR_CUDA(cudaMemcpyAsync(sv->h_results, sv->d_results, 2 * runs.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                          sv->stream));
+  PR_CUDA(cudaStreamSynchronize(sv->stream));
+  double e = 0.0;
+  for (size_t r = 0; r < runs.size(); ++r) e += sv->h_results[2 * r];
+  if (energy) *energy = e;
+  if (norm2) *norm2 = sv->h_results[1];
+  return SV_OK;
+}
+
+// every run is padded to the same coset dimension D = min(kExpD, n)
+template <typename R, typename Idx>
+int run_expval_d(sv_state *sv, int d, const std::vector<HostExpRun> &runs,
+                 const std::vector<const ExpGroupDev *> &dg, const std::vector<const ExpTermDev *> &dt,
+                 double *energy, double *norm2) {
+  switch (d) {
+    case 1: return run_expval_t<R, Idx, 1>(sv, runs, dg, dt, energy, norm2);
+    case 2: return run_expval_t<R, Idx, 2>(sv, runs, dg, dt, energy, norm2);
+    case 3: return run_expval_t<R, Idx, 3>(sv, runs, dg, dt, energy, norm2);
+    default: return run_expval_t<R, Idx, kExpD>(sv, runs, dg, dt, energy, norm2);
+  }
+}
+
+// pad every run's basis to the kernel's fixed dimension with unused index bits
+void pad_runs(int n, int D, std::vector<HostExpRun> &runs) {
+  for (auto &r : runs) {
+    int d = r.dev.d;
+    uint64_t used = 0;
+    for (int b = 0; b < d; ++b) used |= 1ULL << r.dev.piv[b];
+    for (int bit = n - 1; bit >= 0 && d < D; --bit) {
+      if ((used >> bit) & 1ULL) continue;
+      // a new unit vector e_bit: it has pivot `bit`; existing basis vectors
+      // with that bit set must drop it to stay reduced
+      uint64_t e = 1ULL << bit;
+      for (int b = 0; b < d; ++b)
+        if ((r.dev.basis[b] >> bit) & 1ULL) r.dev.basis[b] ^= e;
+      int pos = d;
+      while (pos > 0 && r.dev.piv[pos - 1] > bit) {
+        r.dev.basis[pos] = r.dev.basis[pos - 1];
+        r.dev.piv[pos] = r.dev.piv[pos - 1];
+        --pos;
+      }
+      r.dev.basis[pos] = e;
+      r.dev.piv[pos] = bit;
+      used |= e;
+      ++d;
+    }
+    r.dev.d = d;
+  }
+}
+
+// recompute u and zt after padding (coordinates change when pivots are added)
+void recode_runs(std::vector<HostExpRun> &runs, const std::vector<std::vector<uint64_t>> &gx) {
+  for (size_t r = 0; r < runs.size(); ++r) {
+    auto &R = runs[r];
+    const int d = R.dev.d;
+    for (size_t g = 0; g < R.groups.size(); ++g) {
+      uint64_t xg = gx[r][g];
+      int u = 0;
+      for (int b = 0; b < d; ++b)
+        if ((xg >> R.dev.piv[b]) & 1ULL) u |= 1 << b;
+      R.groups[g].u = u;
+      for (int j = R.groups[g].first; j < R.groups[g].first + R.groups[g].count; ++j) {
+        uint32_t zt = 0;
+        for (int l = 0; l < (1 << d); ++l) {
+          uint64_t s = 0;
+          for (int b = 0; b < d; ++b)
+            if ((l >> b) & 1) s ^= R.dev.basis[b];
+          zt |= (uint32_t)(popc64(s & R.terms[j].z) & 1) << l;
+        }
+        R.terms[j].zt = zt;
+      }
+    }
+  }
+}
+
+int prepare(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c, size_t count, int mode,
+            std::vector<HostExpRun> &runs, int &D) {
+  if (count && (!x || !z || !c)) return fail(SV_EINVAL, "NULL term arrays");
+  int rc = validate_masks(sv->n, x, z, count);
+  if (rc) return rc;
+  for (size_t j = 0; j < count; ++j)
+    if (!std::isfinite(c[j])) return fail(SV_EINVAL, "coefficient %zu is not finite", j);
+  plan_groups(sv, x, z, c, count, mode, runs);
+  // remember each group's x before padding changes the basis
+  std::vector<std::vector<uint64_t>> gx(runs.size());
+  {
+    // rebuild x per group from the basis and u (valid before padding)
+    for (size_t r = 0; r < runs.size(); ++r) {
+      for (auto &G : runs[r].groups) {
+        uint64_t v = 0;
+        for (int b = 0; b < runs[r].dev.d; ++b)
+          if ((G.u >> b) & 1) v ^= runs[r].dev.basis[b];
+        gx[r].push_back(v);
+      }
+    }
+  }
+  D = std::min(kExpD, sv->n);
+  pad_runs(sv->n, D, runs);
+  recode_runs(runs, gx);
+  return SV_OK;
+}
+
+}  // namespace
+
+int expval_impl(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c, size_t count,
+                double *energy, double *norm2) {
+  std::vector<HostExpRun> runs;
+  int D = 0;
+  int rc = prepare(sv, x, z, c, count, 0, runs, D);
+  if (rc) return rc;
+  std::vector<const ExpGroupDev *> dg;
+  std::vector<const ExpTermDev *> dt;
+  rc = stage_runs(sv, runs, dg, dt);
+  if (rc) return rc;
+  const bool narrow = sv->n <= 31;
+  if (sv->dtype == SV_C128)
+    return narrow ? run_expval_d<double, uint32_t>(sv, D, runs, dg, dt, energy, norm2)
+                  : run_expval_d<double, uint64_t>(sv, D, runs, dg, dt, energy, norm2);
+  return narrow ? run_expval_d<float, uint32_t>(sv, D, runs, dg, dt, energy, norm2)
+                : run_expval_d<float, uint64_t>(sv, D, runs, dg, dt, energy, norm2);
+}
+
+template <typename R, typename Idx, int D>
+static int run_pauli_sum_t(sv_state *dst, sv_state *src, const std::vector<HostExpRun> &runs,
+                           const std::vector<const ExpGroupDev *> &dg, const std::vector<const ExpTermDev *> &dt) {
+  using C = typename Cx<R>::T;
+  static int cap = 0;
+  if (!cap) cap = occ_blocks(k_pauli_sum<R, Idx, D>);
+  const uint64_t n_cosets = (1ULL << src->n) >> D;
+  uint64_t need = (n_cosets + kThreads - 1) / kThreads;
+  int blocks = (int)(need < (uint64_t)cap ? need : (uint64_t)cap);
+  if (blocks < 1) blocks = 1;
+  PR_CUDA(cudaMemsetAsync(dst->amps, 0, amp_bytes(dst->dtype) << dst->n, src->stream));
+  for (size_t r = 0; r < runs.size(); ++r) {
+    const int tr = trace_begin(src);
+    k_pauli_sum<R, Idx, D><<<blocks, kThreads, 0, src->stream>>>((C *)dst->amps, (const C *)src->amps,
+                                                                    (Idx)n_cosets, runs[r].dev, dg[r], dt[r]);
+    PR_CHECK_LAUNCH();
+    trace_end(src, tr, KN_PAULI_SUM, 3.0 * (double)sizeof(C) * (double)(1ULL << src->n));
+  }
+  return SV_OK;
+}
+
+template <typename R, typename Idx>
+static int pauli_sum_d(sv_state *dst, sv_state *src, int D, const std::vector<HostExpRun> &runs,
+                       const std::vector<const ExpGroupDev *> &dg, const std::vector<const ExpTermDev *> &dt) {
+  switch (D) {
+    case 1: return run_pauli_sum_t<R, Idx, 1>(dst, src, runs, dg, dt);
+    case 2: return run_pauli_sum_t<R, Idx, 2>(dst, src, runs, dg, dt);
+    case 3: return run_pauli_sum_t<R, Idx, 3>(dst, src, runs, dg, dt);
+    default: return run_pauli_sum_t<R, Idx, kExpD>(dst, src, runs, dg, dt);
+  }
+}
+
+static int dispatch_pauli_sum(sv_state *dst, sv_state *src, int D, const std::vector<HostExpRun> &runs,
+                              const std::vector<const ExpGroupDev *> &dg, const std::vector<const ExpTermDev *> &dt) {
+  const bool narrow = src->n <= 31;
+  if (src->dtype == SV_C128)
+    return narrow ? pauli_sum_d<double, uint32_t>(dst, src, D, runs, dg, dt)
+                  : pauli_sum_d<double, uint64_t>(dst, src, D, runs, dg, dt);
+  return narrow ? pauli_sum_d<float, uint32_t>(dst, src, D, runs, dg, dt)
+                : pauli_sum_d<float, uint64_t>(dst, src, D, runs, dg, dt);
+}
+
+int pauli_sum_impl(sv_state *dst, sv_state *src, const uint64_t *x, const uint64_t *z, const double *c,
+                   size_t count) {
+  if (!dst || !src) return fail(SV_EINVAL, "NULL state");
+  if (dst == src || dst->amps == src->amps) return fail(SV_EINVAL, "dst must differ from src");
+  if (dst->n != src->n || dst->dtype != src->dtype) return fail(SV_EINVAL, "shape mismatch");
+  std::vector<HostExpRun> runs;
+  int D = 0;
+  int rc = prepare(src, x, z, c, count, 1, runs, D);
+  if (rc) return rc;
+  std::vector<const ExpGroupDev *> dg;
+  std::vector<const ExpTermDev *> dt;
+  rc = stage_runs(src, runs, dg, dt);
+  if (rc) return rc;
+  // dst work is ordered on src's stream; make dst's stream wait for it
+  rc = dispatch_pauli_sum(dst, src, D, runs, dg, dt);
+  if (rc) return rc;
+  if (dst->stream != src->stream) PR_CUDA(cudaStreamSynchronize(src->stream));
+  dst->frame = Pauli();
+  return SV_OK;
+}
+
+}  // namespace pr
+
+using namespace pr;
+
+extern "C" {
+
+int expval_pauli_sum(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *coeff, size_t count,
+                     double *out_energy, double *out_norm2) {
+  if (!sv) return fail(SV_EINVAL, "sv is NULL");
+  if (!out_energy) return fail(SV_EINVAL, "out_energy is NULL");
+  return expval_impl(sv, x, z, coeff, count, out_energy, out_norm2);
+}
+
+int apply_pauli_sum(sv_state *dst, sv_state *src, const uint64_t *x, const uint64_t *z, const double *coeff,
+                    size_t count) {
+  return pauli_sum_impl(dst, src, x, z, coeff, count);
+}
+
+}  // extern "C"

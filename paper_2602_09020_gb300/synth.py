@@ -218,7 +218,8 @@ def jw_hamiltonian(n: int, n_terms: int, seed: int, *, sigma: float = 0.5,
         p, q = pairs[k]
         groups.append(("hop", (p, q)))
     left = remaining - 2 * n_hop
-    n_dbl = left // 8
+    n_quads = n * (n - 1) * (n - 2) * (n - 3) // 24
+    n_dbl = min(left // 8, n_quads // 2)
     tail = left - 8 * n_dbl
     quads = set()
     while len(quads) < n_dbl:
@@ -239,14 +240,24 @@ def jw_hamiltonian(n: int, n_terms: int, seed: int, *, sigma: float = 0.5,
         emit(x, z, c, kind)
     # pad to exactly n_terms with fresh hopping-type strings carrying one extra Z
     # (the shape of JW one-body terms dressed by a number operator)
+    # (small n: any unused string once those run out)
+    attempts = 0
     while tail > 0:
-        p, q = sorted(g.choice(n, size=2, replace=False).tolist())
-        r = int(g.integers(0, n))
-        x = (1 << p) | (1 << q)
-        z = _chain(p, q) ^ ((1 << r) if r not in (p, q) else 0)
-        if (x, z) in seen:
+        attempts += 1
+        if attempts > 64 * n_terms + 4096:
+            raise ValueError(f"cannot draw {n_terms} distinct strings on {n} qubits")
+        if attempts <= 16 * n_terms:
+            p, q = sorted(g.choice(n, size=2, replace=False).tolist())
+            r = int(g.integers(0, n))
+            x = (1 << p) | (1 << q)
+            z = _chain(p, q) ^ ((1 << r) if r not in (p, q) else 0)
+            kind = "hopz"
+        else:
+            x, z = int(g.integers(0, 1 << n)), int(g.integers(0, 1 << n))
+            kind = "any"
+        if (x, z) in seen or (x == 0 and z == 0):
             continue
-        emit(x, z, g.normal(0.0, sigma), "hopz")
+        emit(x, z, g.normal(0.0, sigma), kind)
         tail -= 1
     return _finish(n, xs, zs, cs, kinds)
 
