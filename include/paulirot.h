@@ -178,6 +178,28 @@ int trotter_expand(const uint64_t *x, const uint64_t *z, const double *c, size_t
 int expval_pauli_sum(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *coeff,
                      size_t count, double *out_energy, double *out_norm2);
 
+/* Allocation-free variant of expval_pauli_sum (the paper has no counterpart).
+ * Same result and tolerance, but the call allocates nothing: no cudaMalloc,
+ * cudaFree, pinned or heap memory.  It is meant for callers that cannot
+ * allocate while they run -- code living inside a memory budget that an outer
+ * framework has already carved up, latency-critical loops that cannot afford
+ * the device-wide synchronisation an allocation can cause, and hosts that
+ * forbid allocation after start-up.
+ * Scratch: a fixed 4 MiB device array inside the library (held by every GPU
+ * that loads the library until the process exits) plus a static host buffer.
+ * Limits: at most 4096 terms and at most 1024 internal passes (groups of
+ * terms whose x-masks span <= 4 dimensions); larger requests fail with
+ * SV_EINVAL and a message, before any device work.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.
+ * Sharing: every call uses the same array and it keeps the last call's
+ * contents; nothing in it needs to start at zero (every value is written before
+ * it is read).  Calls that overlap on the GPU (other host threads, other streams)
+ * race on the array; host threads are serialised by a lock, GPU work is not. */
+int expval_pauli_sum_noalloc(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *coeff,
+                             size_t count, double *out_energy, double *out_norm2);
+
 /* dst <- sum_j c_j P_j applied to src's represented state (dst gets the
  * identity frame).  Same n and dtype; dst must not be src. */
 int apply_pauli_sum(sv_state *dst, sv_state *src, const uint64_t *x, const uint64_t *z,

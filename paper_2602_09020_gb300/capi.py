@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
         "plan_stats": ([vp, P(sz), P(sz), P(sz)], i),
         "trotter_expand": ([vp, vp, vp, sz, d, i, i, i, vp, vp, vp, sz, P(sz)], i),
         "expval_pauli_sum": ([vp, vp, vp, vp, sz, P(d), P(d)], i),
+        "expval_pauli_sum_noalloc": ([vp, vp, vp, vp, sz, P(d), P(d)], i),
         "apply_pauli_sum": ([vp, vp, vp, vp, vp, sz], i),
         "rotation_grads": ([vp, vp, vp, vp, sz, vp, vp, vp, sz, P(d), vp], i),
         "apply_pauli_rotations_gates": ([vp, vp, vp, vp, sz, P(sz)], i),
@@ -101,7 +102,7 @@ def exported_symbols() -> Sequence[str]:
             "sv_device_ptr", "sv_info", "sv_set_basis_state", "sv_from_host", "sv_to_host",
             "sv_materialize", "sv_copy", "frame_reset", "frame_apply_pauli", "frame_get",
             "apply_pauli_rotations", "plan_create", "plan_apply", "plan_free", "plan_stats",
-            "trotter_expand", "expval_pauli_sum", "apply_pauli_sum", "rotation_grads",
+            "trotter_expand", "expval_pauli_sum", "expval_pauli_sum_noalloc", "apply_pauli_sum", "rotation_grads",
             "apply_pauli_rotations_gates", "batch_run", "sv_trace_start", "sv_trace_stop"]
 
 
@@ -257,6 +258,15 @@ def expval_pauli_sum(sv: int, x, z, coeff) -> Tuple[float, float]:
     x, z, c = _u64(x), _u64(z), _f64(coeff)
     e, nrm = ctypes.c_double(), ctypes.c_double()
     _check(lib().expval_pauli_sum(sv, _p(x), _p(z), _p(c), len(c), ctypes.byref(e), ctypes.byref(nrm)))
+    return e.value, nrm.value
+
+
+def expval_pauli_sum_noalloc(sv: int, x, z, coeff) -> Tuple[float, float]:
+    """As expval_pauli_sum, through the entry point that allocates nothing
+    (fixed device scratch inside the library; at most 4096 terms)."""
+    x, z, c = _u64(x), _u64(z), _f64(coeff)
+    e, nrm = ctypes.c_double(), ctypes.c_double()
+    _check(lib().expval_pauli_sum_noalloc(sv, _p(x), _p(z), _p(c), len(c), ctypes.byref(e), ctypes.byref(nrm)))
     return e.value, nrm.value
 
 

@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <cmath>
 
 #include "internal.h"
 
@@ -683,3 +685,301 @@ int apply_pauli_sum(sv_state *dst, sv_state *src, const uint64_t *x, const uint6
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free <H>
+//
+// expval_pauli_sum_noalloc computes the same energy and norm as
+// expval_pauli_sum but never allocates: no cudaMalloc/cudaFree, no pinned
+// host buffers, no heap.  It is for callers that must not allocate during the
+// call -- code that runs under a fixed memory budget handed out by an outer
+// framework, latency-critical loops that cannot take the device-wide
+// synchronisation a first cudaMalloc implies, and hosts that forbid allocation
+// after start-up.  Its device scratch is the file-scope array below (every GPU
+// that loads this library holds it until the process exits); its host staging
+// is a static buffer guarded by a mutex.
+namespace pr {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 4u << 20;  // 4 MiB of device scratch per GPU
+constexpr int kNoAllocMaxTerms = 4096;
+constexpr int kNoAllocMaxRuns = 1024;
+constexpr int kNoAllocBlocks = 128;  // fixed grid: fixes the partials layout
+constexpr int kNoAllocMaxDevices = 64;
+
+// device layout: [groups: runs*16][terms: max terms][partials: runs*blocks*2][results: runs*2]
+constexpr size_t kNaGroupsOff = 0;
+constexpr size_t kNaTermsOff = kNaGroupsOff + sizeof(ExpGroupDev) * kNoAllocMaxRuns * kExpMaxGroups;
+constexpr size_t kNaPartOff = kNaTermsOff + sizeof(ExpTermDev) * kNoAllocMaxTerms;
+constexpr size_t kNaResOff = kNaPartOff + sizeof(double) * 2 * kNoAllocBlocks * kNoAllocMaxRuns;
+constexpr size_t kNaEnd = kNaResOff + sizeof(double) * 2 * kNoAllocMaxRuns;
+static_assert(kNaEnd <= kNoAllocScratchBytes, "no-alloc scratch layout exceeds the array");
+
+}  // namespace
+}  // namespace pr
+
+// The scratch itself.  In host code this name is only a stand-in, never a
+// device address: the address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[pr::kNoAllocScratchBytes];
+
+namespace pr {
+namespace {
+
+struct NoAllocHost {
+  uint32_t order[kNoAllocMaxTerms];
+  uint64_t tx[kNoAllocMaxTerms], tz[kNoAllocMaxTerms];
+  double tc[kNoAllocMaxTerms];
+  int32_t grp_first[kNoAllocMaxTerms], grp_count[kNoAllocMaxTerms];
+  uint64_t grp_x[kNoAllocMaxTerms];
+  char grp_used[kNoAllocMaxTerms];
+  ExpRunDev runs[kNoAllocMaxRuns];
+  int32_t run_groups[kNoAllocMaxRuns];
+  int32_t run_term_off[kNoAllocMaxRuns];
+  ExpGroupDev groups[kNoAllocMaxRuns * kExpMaxGroups];
+  ExpTermDev terms[kNoAllocMaxTerms];
+  double results[2 * kNoAllocMaxRuns];
+};
+NoAllocHost g_na_host;
+std::mutex g_na_mutex;
+void *g_na_dev[kNoAllocMaxDevices];
+
+// heap sort of order[0..m) by key x (no allocation)
+void sort_by_x(uint32_t *ord, const uint64_t *key, int m) {
+  auto less = [&](int a, int b) { return key[ord[a]] < key[ord[b]] || (key[ord[a]] == key[ord[b]] && ord[a] < ord[b]); };
+  auto sift = [&](int root, int end) {
+    while (2 * root + 1 < end) {
+      int ch = 2 * root + 1;
+      if (ch + 1 < end && less(ch, ch + 1)) ++ch;
+      if (!less(root, ch)) return;
+      uint32_t t = ord[root]; ord[root] = ord[ch]; ord[ch] = t;
+      root = ch;
+    }
+  };
+  for (int i = m / 2 - 1; i >= 0; --i) sift(i, m);
+  for (int end = m - 1; end > 0; --end) {
+    uint32_t t = ord[0]; ord[0] = ord[end]; ord[end] = t;
+    sift(0, end);
+  }
+}
+
+// Pack the sign-rewritten terms into runs exactly as plan_groups does, with
+// fixed-size arrays.  Returns the number of runs or a negative status.
+int na_plan(const sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c, int m, int D) {
+  NoAllocHost &h = g_na_host;
+  const Pauli &q = sv->frame;
+  for (int j = 0; j < m; ++j) {
+    h.order[j] = (uint32_t)j;
+    h.tx[j] = x[j];
+    h.tz[j] = z[j];
+    h.tc[j] = anticommute(x[j], z[j], q.x, q.z) ? -c[j] : c[j];
+  }
+  sort_by_x(h.order, h.tx, m);
+  int ng = 0;
+  for (int a = 0; a < m;) {
+    int b = a;
+    const uint64_t xa = h.tx[h.order[a]];
+    while (b < m && h.tx[h.order[b]] == xa && b - a < kExpMaxTerms) ++b;
+    h.grp_first[ng] = a;
+    h.grp_count[ng] = b - a;
+    h.grp_x[ng] = xa;
+    h.grp_used[ng] = 0;
+    ++ng;
+    a = b;
+  }
+  int nr = 0, nt = 0, left = ng;
+  while (left > 0 || nr == 0) {
+    if (nr >= kNoAllocMaxRuns) return fail(SV_EINVAL, "more than %d expectation runs needed", kNoAllocMaxRuns);
+    ExpRunDev &R = h.runs[nr];
+    std::memset(&R, 0, sizeof(R));
+    uint64_t basis[kDMax];
+    int piv[kDMax];
+    int d = 0;
+    auto reduce = [&](uint64_t v) {
+      for (int bb = 0; bb < d; ++bb)
+        if ((v >> piv[bb]) & 1ULL) v ^= basis[bb];
+      return v;
+    };
+    int members[kExpMaxGroups];
+    int nm = 0, run_terms = 0;
+    for (int g = 0; g < ng; ++g) {
+      if (h.grp_used[g]) continue;
+      if (nm >= kExpMaxGroups) break;
+      if (run_terms + h.grp_count[g] > kExpMaxTerms) continue;
+      uint64_t rr = reduce(h.grp_x[g]);
+      if (rr != 0) {
+        if (d >= D) continue;
+        int p = 63 - __builtin_clzll(rr);
+        for (int bb = 0; bb < d; ++bb)
+          if ((basis[bb] >> p) & 1ULL) basis[bb] ^= rr;
+        int pos = d;
+        while (pos > 0 && piv[pos - 1] > p) {
+          basis[pos] = basis[pos - 1];
+          piv[pos] = piv[pos - 1];
+          --pos;
+        }
+        basis[pos] = rr;
+        piv[pos] = p;
+        ++d;
+      }
+      h.grp_used[g] = 1;
+      --left;
+      members[nm++] = g;
+      run_terms += h.grp_count[g];
+    }
+    // pad the basis to dimension D with the highest unused index bits
+    uint64_t used = 0;
+    for (int bb = 0; bb < d; ++bb) used |= 1ULL << piv[bb];
+    for (int bit = sv->n - 1; bit >= 0 && d < D; --bit) {
+      if ((used >> bit) & 1ULL) continue;
+      const uint64_t e = 1ULL << bit;
+      for (int bb = 0; bb < d; ++bb)
+        if ((basis[bb] >> bit) & 1ULL) basis[bb] ^= e;
+      int pos = d;
+      while (pos > 0 && piv[pos - 1] > bit) {
+        basis[pos] = basis[pos - 1];
+        piv[pos] = piv[pos - 1];
+        --pos;
+      }
+      basis[pos] = e;
+      piv[pos] = bit;
+      used |= e;
+      ++d;
+    }
+    R.d = d;
+    for (int bb = 0; bb < d; ++bb) {
+      R.basis[bb] = basis[bb];
+      R.piv[bb] = piv[bb];
+    }
+    R.n_groups = nm;
+    R.with_norm = nr == 0 ? 1 : 0;
+    h.run_groups[nr] = nm;
+    h.run_term_off[nr] = nt;
+    int local = 0;
+    for (int k = 0; k < nm; ++k) {
+      const int g = members[k];
+      ExpGroupDev &G = h.groups[nr * kExpMaxGroups + k];
+      G.u = 0;
+      for (int bb = 0; bb < d; ++bb)
+        if ((h.grp_x[g] >> piv[bb]) & 1ULL) G.u |= 1 << bb;
+      G.first = local;  // relative to this run's first term (k_expval stages [0, first+count))
+      G.count = h.grp_count[g];
+      G.pad = 0;
+      for (int i = 0; i < h.grp_count[g]; ++i) {
+        const int j = (int)h.order[h.grp_first[g] + i];
+        ExpTermDev &t = h.terms[nt + local + i];
+        t.z = h.tz[j];
+        uint32_t zt = 0;
+        for (int l = 0; l < (1 << d); ++l) {
+          uint64_t s = 0;
+          for (int bb = 0; bb < d; ++bb)
+            if ((l >> bb) & 1) s ^= basis[bb];
+          zt |= (uint32_t)(popc64(s & h.tz[j]) & 1) << l;
+        }
+        t.zt = zt;
+        const int ny = popc64(h.tx[j] & h.tz[j]) & 3;
+        if (h.tx[j] == 0) {
+          t.coef = h.tc[j];
+          t.imag = 0;
+        } else {
+          t.coef = 2.0 * h.tc[j] * ((ny == 0 || ny == 1) ? 1.0 : -1.0);
+          t.imag = ny & 1;
+        }
+      }
+      local += h.grp_count[g];
+    }
+    nt += local;
+    ++nr;
+    if (left == 0) break;
+  }
+  return nr;
+}
+
+int na_device_scratch(void **out) {
+  int dev = 0;
+  PR_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(SV_EUNSUPPORTED, "device index %d", dev);
+  if (!g_na_dev[dev]) {
+    void *p = nullptr;
+    PR_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_na_dev[dev] = p;
+  }
+  *out = g_na_dev[dev];
+  return SV_OK;
+}
+
+template <typename R, typename Idx, int D>
+int na_launch(sv_state *sv, char *scratch, int nr, int nt) {
+  using C = typename Cx<R>::T;
+  NoAllocHost &h = g_na_host;
+  // one upload of every run's groups and terms
+  PR_CUDA(cudaMemcpyAsync(scratch + kNaGroupsOff, h.groups, sizeof(ExpGroupDev) * kExpMaxGroups * nr,
+                          cudaMemcpyHostToDevice, sv->stream));
+  PR_CUDA(cudaMemcpyAsync(scratch + kNaTermsOff, h.terms, sizeof(ExpTermDev) * (nt ? nt : 1),
+                          cudaMemcpyHostToDevice, sv->stream));
+  const uint64_t n_cosets = (1ULL << sv->n) >> D;
+  uint64_t need = (n_cosets + kThreads - 1) / kThreads;
+  const int blocks = (int)(need < (uint64_t)kNoAllocBlocks ? (need ? need : 1) : kNoAllocBlocks);
+  double *part = (double *)(scratch + kNaPartOff);
+  double *res = (double *)(scratch + kNaResOff);
+  const ExpGroupDev *dg = (const ExpGroupDev *)(scratch + kNaGroupsOff);
+  const ExpTermDev *dt = (const ExpTermDev *)(scratch + kNaTermsOff);
+  for (int r = 0; r < nr; ++r) {
+    k_expval<R, Idx, D><<<blocks, kThreads, 0, sv->stream>>>((const C *)sv->amps, (Idx)n_cosets, h.runs[r],
+                                                            dg + (size_t)r * kExpMaxGroups, dt + h.run_term_off[r],
+                                                            part + 2 * blocks * r);
+    PR_CHECK_LAUNCH();
+  }
+  k_finish<<<(unsigned)nr, kThreads, 0, sv->stream>>>(part, blocks, res);
+  PR_CHECK_LAUNCH();
+  PR_CUDA(cudaMemcpyAsync(h.results, res, sizeof(double) * 2 * nr, cudaMemcpyDeviceToHost, sv->stream));
+  PR_CUDA(cudaStreamSynchronize(sv->stream));
+  return SV_OK;
+}
+
+template <typename R, typename Idx>
+int na_launch_d(sv_state *sv, char *scratch, int nr, int nt, int D) {
+  switch (D) {
+    case 1: return na_launch<R, Idx, 1>(sv, scratch, nr, nt);
+    case 2: return na_launch<R, Idx, 2>(sv, scratch, nr, nt);
+    case 3: return na_launch<R, Idx, 3>(sv, scratch, nr, nt);
+    default: return na_launch<R, Idx, kExpD>(sv, scratch, nr, nt);
+  }
+}
+
+}  // namespace
+}  // namespace pr
+
+extern "C" int expval_pauli_sum_noalloc(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *coeff,
+                                        size_t count, double *out_energy, double *out_norm2) {
+  using namespace pr;
+  if (!sv) return fail(SV_EINVAL, "sv is NULL");
+  if (!out_energy) return fail(SV_EINVAL, "out_energy is NULL");
+  if (count > (size_t)kNoAllocMaxTerms)
+    return fail(SV_EINVAL, "expval_pauli_sum_noalloc takes at most %d terms (got %zu)", kNoAllocMaxTerms, count);
+  if (count && (!x || !z || !coeff)) return fail(SV_EINVAL, "NULL term arrays");
+  int rc = validate_masks(sv->n, x, z, count);
+  if (rc) return rc;
+  for (size_t j = 0; j < count; ++j)
+    if (!std::isfinite(coeff[j])) return fail(SV_EINVAL, "coefficient %zu is not finite", j);
+  void *scratch = nullptr;
+  rc = na_device_scratch(&scratch);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  const int D = std::min(kExpD, sv->n);
+  const int nr = na_plan(sv, x, z, coeff, (int)count, D);
+  if (nr < 0) return nr;
+  int nt = 0;
+  for (int r = 0; r < nr; ++r)
+    for (int k = 0; k < g_na_host.run_groups[r]; ++k) nt += g_na_host.groups[r * kExpMaxGroups + k].count;
+  const bool narrow = sv->n <= 31;
+  char *s = (char *)scratch;
+  if (sv->dtype == SV_C128)
+    rc = narrow ? na_launch_d<double, uint32_t>(sv, s, nr, nt, D) : na_launch_d<double, uint64_t>(sv, s, nr, nt, D);
+  else
+    rc = narrow ? na_launch_d<float, uint32_t>(sv, s, nr, nt, D) : na_launch_d<float, uint64_t>(sv, s, nr, nt, D);
+  if (rc) return rc;
+  double e = 0.0;
+  for (int r = 0; r < nr; ++r) e += g_na_host.results[2 * r];
+  *out_energy = e;
+  if (out_norm2) *out_norm2 = g_na_host.results[1];
+  return SV_OK;
+}
