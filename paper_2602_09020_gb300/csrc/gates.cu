@@ -24,42 +24,43 @@ struct Cx<double> {
   using T = double2;
 };
 
-// one-qubit 2x2 gate [[m00, m01], [m10, m11]] (complex entries) on qubit q
+// Hadamard on qubit q, in the amplitude precision
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-    k_gate1(typename Cx<R>::T *__restrict__ amp, uint64_t half, int q, double2 m00, double2 m01, double2 m10,
-            double2 m11) {
+    k_hadamard(typename Cx<R>::T *__restrict__ amp, uint64_t half, int q) {
   using C = typename Cx<R>::T;
+  const R r = (R)0.70710678118654752440;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t lowmask = (1ULL << q) - 1ULL;
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < half; t += stride) {
     const uint64_t k0 = ((t >> q) << (q + 1)) | (t & lowmask), k1 = k0 | (1ULL << q);
     const C a = amp[k0], b = amp[k1];
     C o0, o1;
-    o0.x = (R)(m00.x * a.x - m00.y * a.y + m01.x * b.x - m01.y * b.y);
-    o0.y = (R)(m00.x * a.y + m00.y * a.x + m01.x * b.y + m01.y * b.x);
-    o1.x = (R)(m10.x * a.x - m10.y * a.y + m11.x * b.x - m11.y * b.y);
-    o1.y = (R)(m10.x * a.y + m10.y * a.x + m11.x * b.y + m11.y * b.x);
+    o0.x = r * (a.x + b.x);
+    o0.y = r * (a.y + b.y);
+    o1.x = r * (a.x - b.x);
+    o1.y = r * (a.y - b.y);
     amp[k0] = o0;
     amp[k1] = o1;
   }
 }
 
-// diagonal one-qubit gate diag(p0, p1)
+// diag(p0, p1) on qubit q (S, Sdg, Rz, global phases), in the amplitude precision
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-    k_diag1(typename Cx<R>::T *__restrict__ amp, uint64_t half, int q, double2 p0, double2 p1) {
+    k_diag1(typename Cx<R>::T *__restrict__ amp, uint64_t half, int q, double2 p0d, double2 p1d) {
   using C = typename Cx<R>::T;
+  const R p0x = (R)p0d.x, p0y = (R)p0d.y, p1x = (R)p1d.x, p1y = (R)p1d.y;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t lowmask = (1ULL << q) - 1ULL;
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < half; t += stride) {
     const uint64_t k0 = ((t >> q) << (q + 1)) | (t & lowmask), k1 = k0 | (1ULL << q);
     const C a = amp[k0], b = amp[k1];
     C o0, o1;
-    o0.x = (R)(p0.x * a.x - p0.y * a.y);
-    o0.y = (R)(p0.x * a.y + p0.y * a.x);
-    o1.x = (R)(p1.x * b.x - p1.y * b.y);
-    o1.y = (R)(p1.x * b.y + p1.y * b.x);
+    o0.x = p0x * a.x - p0y * a.y;
+    o0.y = p0x * a.y + p0y * a.x;
+    o1.x = p1x * b.x - p1y * b.y;
+    o1.y = p1x * b.y + p1y * b.x;
     amp[k0] = o0;
     amp[k1] = o1;
   }
@@ -87,13 +88,13 @@ struct GateCtx {
   size_t launched = 0;
 };
 
-int gate1(GateCtx &g, int q, double2 m00, double2 m01, double2 m10, double2 m11) {
+int hadamard(GateCtx &g, int q) {
   const uint64_t half = (1ULL << g.sv->n) >> 1;
   const int tr = trace_begin(g.sv);
   if (g.sv->dtype == SV_C128)
-    k_gate1<double><<<g.blocks_half, kThreads, 0, g.sv->stream>>>((double2 *)g.sv->amps, half, q, m00, m01, m10, m11);
+    k_hadamard<double><<<g.blocks_half, kThreads, 0, g.sv->stream>>>((double2 *)g.sv->amps, half, q);
   else
-    k_gate1<float><<<g.blocks_half, kThreads, 0, g.sv->stream>>>((float2 *)g.sv->amps, half, q, m00, m01, m10, m11);
+    k_hadamard<float><<<g.blocks_half, kThreads, 0, g.sv->stream>>>((float2 *)g.sv->amps, half, q);
   PR_CHECK_LAUNCH();
   trace_end(g.sv, tr, KN_GATE1, 4.0 * (double)amp_bytes(g.sv->dtype) * (double)half);
   ++g.launched;
@@ -157,8 +158,6 @@ int apply_pauli_rotations_gates(sv_state *sv, const uint64_t *x, const uint64_t 
   g.sv = sv;
   g.blocks_half = blocks_for((1ULL << sv->n) >> 1);
   g.blocks_quarter = blocks_for((1ULL << sv->n) >> 2);
-  const double r = 1.0 / std::sqrt(2.0);
-  const double2 hp = make_double2(r, 0.0), hm = make_double2(-r, 0.0), z0 = make_double2(0.0, 0.0);
   const double2 one = make_double2(1.0, 0.0), pi_ = make_double2(0.0, 1.0), mi = make_double2(0.0, -1.0);
   const Pauli q = sv->frame;
   int sup[64];
@@ -179,9 +178,9 @@ int apply_pauli_rotations_gates(sv_state *sv, const uint64_t *x, const uint64_t 
       const bool xb = (x[j] >> b) & 1ULL, zb = (z[j] >> b) & 1ULL;
       if (xb && zb) {
         if ((rc = diag1(g, b, one, mi))) return rc;  // Sdg
-        if ((rc = gate1(g, b, hp, hp, hp, hm))) return rc;
+        if ((rc = hadamard(g, b))) return rc;
       } else if (xb) {
-        if ((rc = gate1(g, b, hp, hp, hp, hm))) return rc;
+        if ((rc = hadamard(g, b))) return rc;
       }
     }
     for (int m = 0; m + 1 < k; ++m)
@@ -195,14 +194,13 @@ int apply_pauli_rotations_gates(sv_state *sv, const uint64_t *x, const uint64_t 
       const int b = sup[m];
       const bool xb = (x[j] >> b) & 1ULL, zb = (z[j] >> b) & 1ULL;
       if (xb && zb) {
-        if ((rc = gate1(g, b, hp, hp, hp, hm))) return rc;
+        if ((rc = hadamard(g, b))) return rc;
         if ((rc = diag1(g, b, one, pi_))) return rc;  // S
       } else if (xb) {
-        if ((rc = gate1(g, b, hp, hp, hp, hm))) return rc;
+        if ((rc = hadamard(g, b))) return rc;
       }
     }
   }
-  (void)z0;
   if (out_gates) *out_gates = g.launched;
   return SV_OK;
 }

@@ -583,10 +583,425 @@ int prepare(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c,
   return SV_OK;
 }
 
+// ------------------------------------------------------------------ complex64: exact fixed-point sums
+//
+// For complex64 amplitudes every product of two components is an exact 48-bit
+// integer times a power of two.  k_expval_fix rounds each product once to the
+// fixed-point grid 2^-S (S = 60 for a normalised state) and sums the integers
+// exactly, per Pauli term, in 64-bit registers; the FP64 coefficients c_j are
+// applied to the exact per-term sums on the host.  Each sum is therefore exact
+// up to 2^-(S+1) per product -- at least as accurate as accumulating the exact
+// products in FP64 -- and independent of summation order.  It runs on the
+// integer pipes instead of GB300's narrow FP64 pipe.  Cosets of a 3-dimensional
+// x-span hold 8 amplitudes per thread; a run carries at most 16 terms.
+
+constexpr int kFixD = 3;
+constexpr int kFixTerms = 16;
+
+struct FixTermDev {
+  uint64_t z;
+  uint32_t psm;  // sign bit per pair slot (or per element for u = 0)
+  int32_t u;
+  int32_t imag;
+  int32_t pad;
+};
+struct FixRunDev {
+  uint64_t basis[kFixD];
+  int32_t piv[kFixD];
+  int32_t d;
+  int32_t nterms;
+  int32_t with_norm;
+};
+
+struct FixComp {
+  int32_t m;  // signed integer mantissa, |m| < 2^24
+  int32_t e;  // value = m * 2^e
+};
+
+__device__ __forceinline__ FixComp fix_split(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const int32_t ex = (int32_t)((b >> 23) & 0xffu);
+  int32_t m = (int32_t)(b & 0x7fffffu);
+  if (ex) m |= 0x800000;
+  FixComp c;
+  c.m = (b >> 31) ? -m : m;
+  c.e = (ex ? ex : 1) - 150;
+  return c;
+}
+
+// round(a * b * 2^S).  The caller picks S so that every component satisfies
+// |x| <= 2^((60 - S)/2) (S = 60 - ceil(log2 <a|a>)), hence a.e + b.e + S <= 14
+// and the shift k below is never negative: one rounding right shift of the
+// exact 48-bit product pre-shifted by 14 (|p| < 2^48, so p << 14 < 2^62).
+__device__ __forceinline__ long long fix_mul(FixComp a, FixComp b, int S) {
+  const long long p = (long long)a.m * (long long)b.m;
+  const int k = min(max(14 - (a.e + b.e + S), 0), 63);
+  return ((p << 14) + ((1LL << k) >> 1)) >> k;
+}
+
+__host__ __device__ constexpr int fix_high_bit(int v) {
+  int h = 0;
+  while (v >> (h + 1)) ++h;
+  return h;
+}
+
+__host__ __device__ constexpr int fix_leader(int p, int H) {
+  return ((p >> H) << (H + 1)) | (p & ((1 << H) - 1));
+}
+
+template <int U>
+__device__ __forceinline__ void fix_products(const FixComp (&re)[1 << kFixD], const FixComp (&im)[1 << kFixD],
+                                             long long (&W)[1 << kFixD], int S) {
+  constexpr int E = 1 << kFixD, PAIRS = E / 2;
+  if (U == 0) {
+#pragma unroll
+    for (int l = 0; l < E; ++l) W[l] = fix_mul(re[l], re[l], S) + fix_mul(im[l], im[l], S);
+  } else {
+    constexpr int H = fix_high_bit(U);
+#pragma unroll
+    for (int p = 0; p < PAIRS; ++p) {
+      const int l = fix_leader(p, H), m = l ^ U;
+      W[p] = fix_mul(re[l], re[m], S) + fix_mul(im[l], im[m], S);           // Re conj(a_l) a_m
+      W[PAIRS + p] = fix_mul(re[l], im[m], S) - fix_mul(im[l], re[m], S);   // Im conj(a_l) a_m
+    }
+  }
+}
+
+__device__ __forceinline__ void fix_dispatch(int u, const FixComp (&re)[1 << kFixD], const FixComp (&im)[1 << kFixD],
+                                             long long (&W)[1 << kFixD], int S) {
+  switch (u) {
+    case 0: fix_products<0>(re, im, W, S); break;
+    case 1: fix_products<1>(re, im, W, S); break;
+    case 2: fix_products<2>(re, im, W, S); break;
+    case 3: fix_products<3>(re, im, W, S); break;
+    case 4: fix_products<4>(re, im, W, S); break;
+    case 5: fix_products<5>(re, im, W, S); break;
+    case 6: fix_products<6>(re, im, W, S); break;
+    case 7: fix_products<7>(re, im, W, S); break;
+    default: break;
+  }
+}
+
+template <typename Idx>
+__global__ void __launch_bounds__(kThreads)
+    k_expval_fix(const float2 *__restrict__ amp, Idx n_cosets, const FixRunDev run,
+                 const FixTermDev *__restrict__ gterms, int S, long long *__restrict__ partials) {
+  constexpr int D = kFixD, E = 1 << D, PAIRS = E / 2, NV = kFixTerms + 1;
+  __shared__ FixTermDev terms[kFixTerms];
+  __shared__ Idx soff[E];
+  // per-term accumulators, one column per thread (conflict-free 8-byte rows)
+  __shared__ long long sacc[NV][kThreads];
+  const int nt = run.nterms;
+  if (threadIdx.x < nt) terms[threadIdx.x] = gterms[threadIdx.x];
+  if (threadIdx.x < E) {
+    uint64_t so = 0;
+    for (int b = 0; b < D; ++b)
+      if ((threadIdx.x >> b) & 1) so ^= run.basis[b];
+    soff[threadIdx.x] = (Idx)so;
+  }
+  for (int j = 0; j < NV; ++j) sacc[j][threadIdx.x] = 0;
+  __syncthreads();
+  long long nrm = 0;
+  const Idx stride = (Idx)gridDim.x * blockDim.x;
+  for (Idx c = (Idx)blockIdx.x * blockDim.x + threadIdx.x; c < n_cosets; c += stride) {
+    Idx rep = c;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const int pv = run.piv[b];
+      rep = ((rep >> pv) << (pv + 1)) | (rep & ((Idx(1) << pv) - 1));
+    }
+    FixComp re[E], im[E];
+#pragma unroll
+    for (int l = 0; l < E; ++l) {
+      const float2 v = amp[rep ^ soff[l]];
+      re[l] = fix_split(v.x);
+      im[l] = fix_split(v.y);
+    }
+    if (run.with_norm) {
+#pragma unroll
+      for (int l = 0; l < E; ++l) nrm += fix_mul(re[l], re[l], S) + fix_mul(im[l], im[l], S);
+    }
+    long long W[E];
+    int cur = -1;
+    for (int j = 0; j < nt; ++j) {
+      const FixTermDev t = terms[j];
+      if (t.u != cur) {
+        cur = t.u;
+        fix_dispatch(t.u, re, im, W, S);
+      }
+      long long sum = 0;
+      if (t.u == 0) {
+#pragma unroll
+        for (int l = 0; l < E; ++l) sum += ((t.psm >> l) & 1u) ? -W[l] : W[l];
+      } else if (t.imag) {
+#pragma unroll
+        for (int q = 0; q < PAIRS; ++q) sum += ((t.psm >> q) & 1u) ? -W[PAIRS + q] : W[PAIRS + q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < PAIRS; ++q) sum += ((t.psm >> q) & 1u) ? -W[q] : W[q];
+      }
+      sacc[j][threadIdx.x] += parity((uint64_t)rep & t.z) ? -sum : sum;
+    }
+  }
+  sacc[kFixTerms][threadIdx.x] = nrm;
+  __syncthreads();
+  // exact block sums: warp w reduces rows w, w + 8, ...
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = w; j < NV; j += (int)(blockDim.x >> 5)) {
+    long long v = 0;
+    for (int i = lane; i < (int)blockDim.x; i += 32) v += sacc[j][i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) partials[(size_t)blockIdx.x * NV + j] = v;
+  }
+}
+
+// results[r][j] = sum over blocks of partials[r][b][j]; one CTA per run
+__global__ void k_finish_fix(const long long *__restrict__ partials, int n_blocks, long long *__restrict__ results) {
+  constexpr int NV = kFixTerms + 1;
+  __shared__ long long red[kThreads / 32];
+  const long long *p = partials + (size_t)blockIdx.x * n_blocks * NV;
+  for (int j = 0; j < NV; ++j) {
+    long long v = 0;
+    for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) v += p[(size_t)b * NV + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long t = 0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+      results[(size_t)blockIdx.x * NV + j] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// |a|^2 estimate in FP32 per thread, FP64 per block: only used to pick S
+__global__ void __launch_bounds__(kThreads) k_norm_est(const float2 *__restrict__ amp, uint64_t n, double *out) {
+  float acc = 0.f;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float2 v = amp[i];
+    acc = fmaf(v.x, v.x, fmaf(v.y, v.y, acc));
+  }
+  double a = acc, b = 0.0;
+  block_sum2(a, b);
+  if (threadIdx.x == 0) out[blockIdx.x] = a;
+}
+
+struct FixRunHost {
+  FixRunDev dev;
+  std::vector<FixTermDev> terms;
+  std::vector<double> coef;
+};
+
+// group by x (frame signs applied), chunk groups to <= kFixTerms, pack chunks
+// into runs of <= kFixTerms terms whose x-masks span <= kFixD dimensions
+void plan_fix(const sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c, size_t count,
+              std::vector<FixRunHost> &runs) {
+  const Pauli &q = sv->frame;
+  std::map<uint64_t, std::vector<Term>> by_x;
+  for (size_t j = 0; j < count; ++j) {
+    double cj = c[j];
+    if (anticommute(x[j], z[j], q.x, q.z)) cj = -cj;
+    by_x[x[j]].push_back({x[j], z[j], cj});
+  }
+  std::vector<std::vector<Term>> chunks;
+  for (auto &kv : by_x)
+    for (size_t a = 0; a < kv.second.size(); a += kFixTerms)
+      chunks.emplace_back(kv.second.begin() + a,
+                          kv.second.begin() + std::min(kv.second.size(), a + (size_t)kFixTerms));
+  std::vector<char> used(chunks.size(), 0);
+  size_t left = chunks.size();
+  while (left > 0 || runs.empty()) {
+    FixRunHost r;
+    std::memset(&r.dev, 0, sizeof(r.dev));
+    uint64_t basis[kFixD];
+    int piv[kFixD];
+    int d = 0;
+    auto reduce = [&](uint64_t v) {
+      for (int b = 0; b < d; ++b)
+        if ((v >> piv[b]) & 1ULL) v ^= basis[b];
+      return v;
+    };
+    auto add_vec = [&](uint64_t rr, uint64_t) {
+      int pv = 63 - __builtin_clzll(rr);
+      for (int b = 0; b < d; ++b)
+        if ((basis[b] >> pv) & 1ULL) basis[b] ^= rr;
+      int pos = d;
+      while (pos > 0 && piv[pos - 1] > pv) {
+        basis[pos] = basis[pos - 1];
+        piv[pos] = piv[pos - 1];
+        --pos;
+      }
+      basis[pos] = rr;
+      piv[pos] = pv;
+      ++d;
+    };
+    std::vector<size_t> members;
+    size_t nterm = 0;
+    for (size_t g = 0; g < chunks.size(); ++g) {
+      if (used[g]) continue;
+      if (nterm + chunks[g].size() > (size_t)kFixTerms) continue;
+      uint64_t rr = reduce(chunks[g][0].x);
+      if (rr != 0) {
+        if (d >= kFixD) continue;
+        add_vec(rr, 0);
+      }
+      used[g] = 1;
+      --left;
+      members.push_back(g);
+      nterm += chunks[g].size();
+      if (nterm == (size_t)kFixTerms) break;
+    }
+    // pad to kFixD with the highest unused bits
+    uint64_t usedbits = 0;
+    for (int b = 0; b < d; ++b) usedbits |= 1ULL << piv[b];
+    for (int bit = sv->n - 1; bit >= 0 && d < kFixD; --bit)
+      if (!((usedbits >> bit) & 1ULL)) {
+        add_vec(1ULL << bit, 0);
+        usedbits |= 1ULL << bit;
+      }
+    r.dev.d = d;
+    for (int b = 0; b < d; ++b) {
+      r.dev.basis[b] = basis[b];
+      r.dev.piv[b] = piv[b];
+    }
+    // terms sorted by u so a run recomputes products only when u changes
+    std::vector<std::pair<int, const Term *>> ts;
+    for (size_t g : members)
+      for (const Term &t : chunks[g]) {
+        int u = 0;
+        for (int b = 0; b < d; ++b)
+          if ((t.x >> piv[b]) & 1ULL) u |= 1 << b;
+        ts.push_back({u, &t});
+      }
+    std::stable_sort(ts.begin(), ts.end(), [](const auto &a1, const auto &b1) { return a1.first < b1.first; });
+    for (auto &ut : ts) {
+      const Term &t = *ut.second;
+      const int u = ut.first;
+      FixTermDev e;
+      e.z = t.z;
+      e.u = u;
+      e.pad = 0;
+      uint32_t psm = 0;
+      auto sgn = [&](int l) {
+        uint64_t so = 0;
+        for (int b = 0; b < d; ++b)
+          if ((l >> b) & 1) so ^= basis[b];
+        return (uint32_t)(popc64(so & t.z) & 1);
+      };
+      const int ny = popc64(t.x & t.z) & 3;
+      if (u == 0) {
+        for (int l = 0; l < (1 << kFixD); ++l) psm |= sgn(l) << l;
+        e.imag = 0;
+        r.coef.push_back(t.c);
+      } else {
+        int H = 0;
+        while (u >> (H + 1)) ++H;
+        for (int p = 0; p < (1 << kFixD) / 2; ++p) psm |= sgn(fix_leader(p, H)) << p;
+        e.imag = ny & 1;
+        r.coef.push_back(2.0 * t.c * ((ny == 0 || ny == 1) ? 1.0 : -1.0));
+      }
+      e.psm = psm;
+      r.terms.push_back(e);
+    }
+    r.dev.nterms = (int32_t)r.terms.size();
+    r.dev.with_norm = runs.empty() ? 1 : 0;
+    runs.push_back(std::move(r));
+    if (left == 0) break;
+  }
+}
+
+template <typename Idx>
+int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *energy, double *norm2) {
+  constexpr int NV = kFixTerms + 1;
+  static int cap = 0;
+  if (!cap) cap = occ_blocks(k_expval_fix<Idx>);
+  const uint64_t n_amps = 1ULL << sv->n;
+  const uint64_t n_cosets = n_amps >> kFixD;
+  uint64_t need = (n_cosets + kThreads - 1) / kThreads;
+  const int blocks = (int)(need < (uint64_t)cap ? (need ? need : 1) : cap);
+  const int est_blocks = 64;
+  // partial sums (int64) and the S estimate share the double scratch
+  int rc = ensure_scratch(sv, (size_t)NV * blocks * runs.size() + est_blocks, NV * runs.size() + est_blocks);
+  if (rc) return rc;
+  // stage terms
+  size_t bytes = 0;
+  std::vector<size_t> off(runs.size());
+  for (size_t r = 0; r < runs.size(); ++r) {
+    off[r] = bytes;
+    bytes += ((runs[r].terms.size() * sizeof(FixTermDev)) + 15) & ~size_t(15);
+  }
+  if (!bytes) bytes = 16;
+  PR_CUDA(cudaStreamSynchronize(sv->stream));
+  rc = ensure_stage(sv, bytes);
+  if (rc) return rc;
+  for (size_t r = 0; r < runs.size(); ++r)
+    if (!runs[r].terms.empty())
+      std::memcpy((char *)sv->h_stage + off[r], runs[r].terms.data(), runs[r].terms.size() * sizeof(FixTermDev));
+  PR_CUDA(cudaMemcpyAsync(sv->d_stage, sv->h_stage, bytes, cudaMemcpyHostToDevice, sv->stream));
+  // choose S from an estimate of <a|a>
+  double *est = sv->d_results + NV * runs.size();
+  {
+    const int tr = trace_begin(sv);
+    k_norm_est<<<est_blocks, kThreads, 0, sv->stream>>>((const float2 *)sv->amps, n_amps, est);
+    PR_CHECK_LAUNCH();
+    trace_end(sv, tr, KN_EXPVAL, 8.0 * (double)n_amps);
+  }
+  PR_CUDA(cudaMemcpyAsync(sv->h_results, est, est_blocks * sizeof(double), cudaMemcpyDeviceToHost, sv->stream));
+  PR_CUDA(cudaStreamSynchronize(sv->stream));
+  double nest = 0.0;
+  for (int i = 0; i < est_blocks; ++i) nest += sv->h_results[i];
+  // S = 60 - ceil(log2 <a|a>) (estimate widened by 1 %): every per-term sum is
+  // bounded by <a|a> 2^S <= 2^60 and no product needs a left shift
+  int S = 60;
+  if (nest * 1.01 > 1.0) S = 60 - (int)std::ceil(std::log2(nest * 1.01));
+  if (S < 8) return fail(SV_EUNSUPPORTED, "state norm %g too large for the fixed-point sums", nest);
+  long long *part = (long long *)sv->d_partials;
+  long long *res = (long long *)sv->d_results;
+  for (size_t r = 0; r < runs.size(); ++r) {
+    const int tr = trace_begin(sv);
+    k_expval_fix<Idx><<<blocks, kThreads, 0, sv->stream>>>(
+        (const float2 *)sv->amps, (Idx)n_cosets, runs[r].dev, (const FixTermDev *)((char *)sv->d_stage + off[r]), S,
+        part + (size_t)NV * blocks * r);
+    PR_CHECK_LAUNCH();
+    trace_end(sv, tr, KN_EXPVAL, 8.0 * (double)n_amps);
+  }
+  {
+    const int tr = trace_begin(sv);
+    k_finish_fix<<<(unsigned)runs.size(), kThreads, 0, sv->stream>>>(part, blocks, res);
+    PR_CHECK_LAUNCH();
+    trace_end(sv, tr, KN_FINISH, 8.0 * NV * blocks * runs.size());
+  }
+  PR_CUDA(cudaMemcpyAsync(sv->h_results, res, NV * runs.size() * sizeof(long long), cudaMemcpyDeviceToHost,
+                          sv->stream));
+  PR_CUDA(cudaStreamSynchronize(sv->stream));
+  const long long *h = (const long long *)sv->h_results;
+  const double unit = std::ldexp(1.0, -S);
+  long double e = 0.0L;
+  for (size_t r = 0; r < runs.size(); ++r)
+    for (size_t j = 0; j < runs[r].coef.size(); ++j) e += (long double)runs[r].coef[j] * (long double)h[r * NV + j];
+  if (energy) *energy = (double)(e * unit);
+  if (norm2) *norm2 = (double)h[kFixTerms] * unit;
+  return SV_OK;
+}
+
 }  // namespace
 
 int expval_impl(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c, size_t count,
                 double *energy, double *norm2) {
+  if (sv->dtype == SV_C64 && sv->n >= kFixD) {
+    if (count && (!x || !z || !c)) return fail(SV_EINVAL, "NULL term arrays");
+    int rc = validate_masks(sv->n, x, z, count);
+    if (rc) return rc;
+    for (size_t j = 0; j < count; ++j)
+      if (!std::isfinite(c[j])) return fail(SV_EINVAL, "coefficient %zu is not finite", j);
+    std::vector<FixRunHost> fr;
+    plan_fix(sv, x, z, c, count, fr);
+    return sv->n <= 31 ? expval_fix_t<uint32_t>(sv, fr, energy, norm2) : expval_fix_t<uint64_t>(sv, fr, energy, norm2);
+  }
   std::vector<HostExpRun> runs;
   int D = 0;
   int rc = prepare(sv, x, z, c, count, 0, runs, D);

@@ -193,6 +193,247 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// ------------------------------------------------------------------ complex64, packed pairs
+//
+// k_coset_c64x2: the same fused pass for complex64 with two adjacent cosets
+// per thread (representatives rep and rep|1, bit 0 not a pivot).  Element l of
+// both cosets lies in one aligned 16-byte float4 (its halves swapped when
+// bit 0 of the element offset is set), so each element is one 16-byte load.
+// Registers hold RE[l] = (re of coset 0, re of coset 1) and IM[l] likewise, and
+// every update is a packed FP32x2 fused multiply-add.  The sign of element l
+// for a rotation is (-1)^{popc(rep & z)} * chi(l) with chi a character of l
+// (chi(l) = prod of S_b over the set bits b of l, S_b = (-1)^{popc(basis_b & z)}),
+// so walking the pair leaders in Gray-code order updates the coefficient with one
+// packed multiply by +-1 per pair instead of a per-element select.
+
+// per-rotation values shared by the CTA: tt[p0 | p1 << 1] = (+-t, +-t) for the
+// two coset parities, S[b] = (s_b, s_b) with s_b = (-1)^{popc(basis_b & z)}
+template <typename Idx>
+struct RotSm2 {
+  Idx z;
+  uint32_t code;
+  float2 tt[4];
+  float2 S[4];
+};
+
+// free-bit index k (0-based among bits != H) -> bit position
+template <int H>
+__device__ __host__ constexpr int free_bit(int k) {
+  return k < H ? k : k + 1;
+}
+// Gray code over the D-1 free bits, mapped to element index bits
+template <int D, int H>
+__device__ __host__ constexpr int gray_leader(int i) {
+  int g = i ^ (i >> 1), l = 0;
+  for (int k = 0; k < D - 1; ++k)
+    if ((g >> k) & 1) l |= 1 << free_bit<H>(k);
+  return l;
+}
+__device__ __host__ constexpr int ctz_c(int v) {
+  int c = 0;
+  while (!(v & 1)) {
+    v >>= 1;
+    ++c;
+  }
+  return c;
+}
+__device__ __host__ constexpr int high_bit(int v) {
+  int h = 0;
+  while (v >> (h + 1)) ++h;
+  return h;
+}
+
+// negated coefficient written inline, so the compiler can fold the sign into
+// the packed FMA instead of carrying a second chain
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+
+// Pair update from the old values of both elements (exact tan form; the
+// compiler keeps copies of the old values where a 2-cycle needs them).
+template <int D, int U, int IMAG>
+__device__ __forceinline__ void apply_x2(float2 (&RE)[1 << D], float2 (&IM)[1 << D], float2 T,
+                                         const float2 (&S)[D > 0 ? D : 1]) {
+  if constexpr (U == 0) {
+    // diagonal: every element, Gray order over all D bits
+#pragma unroll
+    for (int i = 0; i < (1 << D); ++i) {
+      if (i > 0) T = __fmul2_rn(T, S[ctz_c(i)]);
+      const int l = i ^ (i >> 1);
+      const float2 re = RE[l], im = IM[l];
+      RE[l] = __ffma2_rn(neg2(T), im, re);
+      IM[l] = __ffma2_rn(T, re, im);
+    }
+  } else {
+    constexpr int H = high_bit(U);
+#pragma unroll
+    for (int i = 0; i < (1 << (D - 1)); ++i) {
+      if (i > 0) T = __fmul2_rn(T, S[free_bit<H>(ctz_c(i))]);
+      const float2 N = neg2(T);
+      const int l = gray_leader<D, H>(i);
+      const int m = l ^ U;
+      const float2 rl = RE[l], il = IM[l], rm = RE[m], im = IM[m];
+      if (IMAG) {
+        RE[l] = __ffma2_rn(N, im, rl);
+        IM[l] = __ffma2_rn(T, rm, il);
+        RE[m] = __ffma2_rn(N, il, rm);
+        IM[m] = __ffma2_rn(T, rl, im);
+      } else {
+        RE[l] = __ffma2_rn(T, rm, rl);
+        IM[l] = __ffma2_rn(T, im, il);
+        RE[m] = __ffma2_rn(N, rl, rm);
+        IM[m] = __ffma2_rn(N, il, im);
+      }
+    }
+  }
+}
+
+#define PR_CASE2(K)                                                                \
+  case K:                                                                          \
+    if constexpr ((((K) >> 1) < (1 << D)) && ((((K) >> 1) != 0) || ((K)&1)))       \
+      apply_x2<D, ((K) >> 1), ((K)&1)>(RE, IM, T, S);                           \
+    break;
+#define PR_CASE2_8(B) \
+  PR_CASE2(B + 0) PR_CASE2(B + 1) PR_CASE2(B + 2) PR_CASE2(B + 3) PR_CASE2(B + 4) PR_CASE2(B + 5) PR_CASE2(B + 6) PR_CASE2(B + 7)
+
+template <int D>
+__device__ __forceinline__ void dispatch_x2(uint32_t code, float2 (&RE)[1 << D], float2 (&IM)[1 << D], float2 T,
+                                            const float2 (&S)[D > 0 ? D : 1]) {
+  switch (code) {
+    PR_CASE2_8(0)
+    PR_CASE2_8(8)
+    PR_CASE2_8(16)
+    PR_CASE2_8(24)
+    default:
+      break;
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename Idx, int D>
+__device__ __forceinline__ Idx pair_rep(Idx c, const RunDev &run) {
+  Idx rep = c << 1;
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    const int p = run.piv[b];
+    rep = ((rep >> p) << (p + 1)) | (rep & ((Idx(1) << p) - 1));
+  }
+  return rep;
+}
+
+// dynamic shared memory: one 16-byte slot per element per thread, laid out
+// [element][thread] so a warp's accesses to one element are contiguous
+template <typename Idx, int D>
+__global__ void __launch_bounds__(kThreads)
+    k_coset_c64x2(float4 *__restrict__ amp4, Idx n_pairs, const RunDev run, const RotDev *__restrict__ rots,
+                  uint64_t fx, uint64_t fz) {
+  extern __shared__ float4 stage[];
+  constexpr int E = 1 << D;
+  __shared__ RotSm2<Idx> srot[kMaxRunRots];
+  __shared__ Idx soff[E];
+  const int count = run.count;
+  for (int j = threadIdx.x; j < count; j += blockDim.x) {
+    const RotDev r = rots[run.first + j];
+    double t = r.t;
+    if (__popcll((r.x & fz) ^ (r.z & fx)) & 1) t = -t;  // runtime frame sign
+    const float tf = (float)t;
+    RotSm2<Idx> s;
+    s.z = (Idx)r.z;
+    s.code = r.code;
+    s.tt[0] = make_float2(tf, tf);
+    s.tt[1] = make_float2(-tf, tf);
+    s.tt[2] = make_float2(tf, -tf);
+    s.tt[3] = make_float2(-tf, -tf);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float sb = (b < D && ((r.zt >> (1 << b)) & 1u)) ? -1.0f : 1.0f;
+      s.S[b] = make_float2(sb, sb);
+    }
+    srot[j] = s;
+  }
+  if (threadIdx.x < E) {
+    uint64_t s = 0;
+    for (int b = 0; b < D; ++b)
+      if ((threadIdx.x >> b) & 1) s ^= run.basis[b];
+    soff[threadIdx.x] = (Idx)s;
+  }
+  __syncthreads();
+
+  const Idx stride = (Idx)gridDim.x * blockDim.x;
+  float4 *slot = stage + threadIdx.x;
+  Idx c = (Idx)blockIdx.x * blockDim.x + threadIdx.x;
+  // prefetch the first coset pair
+  if (c < n_pairs) {
+    const Idx rep0 = pair_rep<Idx, D>(c, run);
+#pragma unroll
+    for (int l = 0; l < E; ++l) cp_async16(slot + l * blockDim.x, amp4 + ((rep0 ^ soff[l]) >> 1));
+    cp_async_commit();
+  }
+  for (; c < n_pairs; c += stride) {
+    const Idx rep = pair_rep<Idx, D>(c, run);
+    cp_async_wait_all();
+    float2 RE[E], IM[E];
+#pragma unroll
+    for (int l = 0; l < E; ++l) {
+      const Idx e = rep ^ soff[l];
+      const float4 v = slot[l * blockDim.x];
+      if (e & 1) {
+        RE[l] = make_float2(v.z, v.x);
+        IM[l] = make_float2(v.w, v.y);
+      } else {
+        RE[l] = make_float2(v.x, v.z);
+        IM[l] = make_float2(v.y, v.w);
+      }
+    }
+    // the slot is free again: prefetch the next coset pair while this one computes
+    const Idx cn = c + stride;
+    if (cn < n_pairs) {
+      const Idx repn = pair_rep<Idx, D>(cn, run);
+#pragma unroll
+      for (int l = 0; l < E; ++l) cp_async16(slot + l * blockDim.x, amp4 + ((repn ^ soff[l]) >> 1));
+      cp_async_commit();
+    }
+    for (int j = 0; j < count; ++j) {
+      const RotSm2<Idx> &s = srot[j];
+      const Idx z = s.z;
+      const int p0 = parity(rep & z);
+      const int q = p0 | ((p0 ^ (int)(z & 1)) << 1);
+      const float2 T = s.tt[q];
+      float2 S[D > 0 ? D : 1];
+#pragma unroll
+      for (int b = 0; b < (D > 0 ? D : 1); ++b) S[b] = s.S[b];
+      dispatch_x2<D>(s.code, RE, IM, T, S);
+    }
+    if (run.fold) {
+      const float fr = (float)run.fold_re, fi = (float)run.fold_im;
+      const float2 FR = make_float2(fr, fr), FI = make_float2(fi, fi), NFI = make_float2(-fi, -fi);
+#pragma unroll
+      for (int l = 0; l < E; ++l) {
+        const float2 re = RE[l], im = IM[l];
+        RE[l] = __ffma2_rn(NFI, im, __fmul2_rn(FR, re));
+        IM[l] = __ffma2_rn(FI, re, __fmul2_rn(FR, im));
+      }
+    }
+    // recompute the element addresses instead of keeping 2^D of them live
+    // across the rotation loop
+    asm volatile("" ::: "memory");
+#pragma unroll
+    for (int l = 0; l < E; ++l) {
+      const Idx e = rep ^ soff[l];
+      float4 v;
+      if (e & 1)
+        v = make_float4(RE[l].y, IM[l].y, RE[l].x, IM[l].x);
+      else
+        v = make_float4(RE[l].x, IM[l].x, RE[l].y, IM[l].y);
+      amp4[e >> 1] = v;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ diagonal phase sums
 
 constexpr int kCls = 1 << kDiagClassBits;  // 16 amplitudes per thread
@@ -219,7 +460,9 @@ __device__ __forceinline__ typename Cx<R>::T turn_phase(uint64_t phi, const type
     s.x = (R)fma(-0.5, x2, 1.0);
     s.y = (R)fma(x2 * (-1.0 / 6.0), x, x);
   } else {
-    const float x = (float)rem * 3.40612158e-19f;
+    // top 32 of the 48 residual bits: a 32-bit conversion (the 64-bit one runs
+    // on the FP64 pipe) is exact enough for float
+    const float x = (float)(uint32_t)(rem >> 16) * 2.23223584e-14f;  // 2 pi / 2^48
     s.x = fmaf(-0.5f * x, x, 1.0f);
     s.y = x;
   }
@@ -309,6 +552,50 @@ int launch_coset_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_
   PR_CHECK_LAUNCH();
   trace_end(sv, tr, KN_COSET0 + D, 2.0 * (double)sizeof(C) * (double)(1ULL << sv->n));
   return SV_OK;
+}
+
+template <typename Idx, int D>
+int launch_c64x2_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t fx, uint64_t fz) {
+  static int cap = 0;
+  const size_t dyn = sizeof(float4) * kThreads * (1u << D);
+  if (!cap) {
+    PR_CUDA(cudaFuncSetAttribute(k_coset_c64x2<Idx, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coset_c64x2<Idx, D>, kThreads, dyn) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    cap = (per_sm > 0 ? per_sm : 1) * device_sm_count();
+  }
+  const uint64_t n_pairs = ((1ULL << sv->n) >> D) >> 1;
+  uint64_t need = (n_pairs + kThreads - 1) / kThreads;
+  unsigned blocks = (unsigned)(need < (uint64_t)cap ? need : (uint64_t)cap);
+  if (!blocks) blocks = 1;
+  const int tr = trace_begin(sv);
+  k_coset_c64x2<Idx, D><<<blocks, kThreads, dyn, sv->stream>>>((float4 *)sv->amps, (Idx)n_pairs, run,
+                                                               plan->d_rots, fx, fz);
+  PR_CHECK_LAUNCH();
+  trace_end(sv, tr, KN_COSET0 + D, 2.0 * 8.0 * (double)(1ULL << sv->n));
+  return SV_OK;
+}
+
+// the packed complex64 pass applies when bit 0 is not a pivot and there are
+// at least two cosets; d = 5 keeps the one-coset kernel (register budget)
+template <typename Idx>
+int launch_c64x2_d(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t fx, uint64_t fz) {
+  switch (run.d) {
+    case 0: return launch_c64x2_t<Idx, 0>(sv, plan, run, fx, fz);
+    case 1: return launch_c64x2_t<Idx, 1>(sv, plan, run, fx, fz);
+    case 2: return launch_c64x2_t<Idx, 2>(sv, plan, run, fx, fz);
+    case 3: return launch_c64x2_t<Idx, 3>(sv, plan, run, fx, fz);
+    case 4: return launch_c64x2_t<Idx, 4>(sv, plan, run, fx, fz);
+    default: return fail(SV_EINVAL, "packed pass: dimension %d", run.d);
+  }
+}
+
+bool use_c64x2(const sv_state *sv, const RunDev &run) {
+  if (sv->dtype != SV_C64 || run.d > 4 || sv->n - run.d < 1) return false;
+  return run.d == 0 || run.piv[0] >= 1;
 }
 
 template <typename R, typename Idx>
@@ -402,6 +689,8 @@ int launch_run(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t fx
                   : launch_diag_t<float, uint64_t>(sv, plan, run, fx);
   }
   if (run.d > sv->n) return fail(SV_EINVAL, "run dimension exceeds n");
+  if (use_c64x2(sv, run))
+    return narrow ? launch_c64x2_d<uint32_t>(sv, plan, run, fx, fz) : launch_c64x2_d<uint64_t>(sv, plan, run, fx, fz);
   if (sv->dtype == SV_C128)
     return narrow ? launch_coset_d<double, uint32_t>(sv, plan, run, fx, fz)
                   : launch_coset_d<double, uint64_t>(sv, plan, run, fx, fz);
