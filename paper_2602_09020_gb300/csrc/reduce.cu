@@ -596,14 +596,15 @@ int prepare(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c,
 // x-span hold 8 amplitudes per thread; a run carries at most 16 terms.
 
 constexpr int kFixD = 3;
-constexpr int kFixTerms = 16;
+constexpr int kFixTerms = 32;
+constexpr int kFixThreads = 128;
 
 struct FixTermDev {
   uint64_t z;
   uint32_t psm;  // sign bit per pair slot (or per element for u = 0)
   int32_t u;
   int32_t imag;
-  int32_t pad;
+  int32_t need;  // parts of conj(a_l) a_m any term of this u needs: 1 = Re, 2 = Im
 };
 struct FixRunDev {
   uint64_t basis[kFixD];
@@ -651,46 +652,54 @@ __host__ __device__ constexpr int fix_leader(int p, int H) {
 
 template <int U>
 __device__ __forceinline__ void fix_products(const FixComp (&re)[1 << kFixD], const FixComp (&im)[1 << kFixD],
-                                             long long (&W)[1 << kFixD], int S) {
+                                             long long (&W)[1 << kFixD], int S, int need) {
   constexpr int E = 1 << kFixD, PAIRS = E / 2;
   if (U == 0) {
 #pragma unroll
     for (int l = 0; l < E; ++l) W[l] = fix_mul(re[l], re[l], S) + fix_mul(im[l], im[l], S);
   } else {
     constexpr int H = fix_high_bit(U);
+    if (need & 1) {
 #pragma unroll
-    for (int p = 0; p < PAIRS; ++p) {
-      const int l = fix_leader(p, H), m = l ^ U;
-      W[p] = fix_mul(re[l], re[m], S) + fix_mul(im[l], im[m], S);           // Re conj(a_l) a_m
-      W[PAIRS + p] = fix_mul(re[l], im[m], S) - fix_mul(im[l], re[m], S);   // Im conj(a_l) a_m
+      for (int p = 0; p < PAIRS; ++p) {
+        const int l = fix_leader(p, H), m = l ^ U;
+        W[p] = fix_mul(re[l], re[m], S) + fix_mul(im[l], im[m], S);  // Re conj(a_l) a_m
+      }
+    }
+    if (need & 2) {
+#pragma unroll
+      for (int p = 0; p < PAIRS; ++p) {
+        const int l = fix_leader(p, H), m = l ^ U;
+        W[PAIRS + p] = fix_mul(re[l], im[m], S) - fix_mul(im[l], re[m], S);  // Im conj(a_l) a_m
+      }
     }
   }
 }
 
-__device__ __forceinline__ void fix_dispatch(int u, const FixComp (&re)[1 << kFixD], const FixComp (&im)[1 << kFixD],
-                                             long long (&W)[1 << kFixD], int S) {
+__device__ __forceinline__ void fix_dispatch(int u, int need, const FixComp (&re)[1 << kFixD],
+                                             const FixComp (&im)[1 << kFixD], long long (&W)[1 << kFixD], int S) {
   switch (u) {
-    case 0: fix_products<0>(re, im, W, S); break;
-    case 1: fix_products<1>(re, im, W, S); break;
-    case 2: fix_products<2>(re, im, W, S); break;
-    case 3: fix_products<3>(re, im, W, S); break;
-    case 4: fix_products<4>(re, im, W, S); break;
-    case 5: fix_products<5>(re, im, W, S); break;
-    case 6: fix_products<6>(re, im, W, S); break;
-    case 7: fix_products<7>(re, im, W, S); break;
+    case 0: fix_products<0>(re, im, W, S, need); break;
+    case 1: fix_products<1>(re, im, W, S, need); break;
+    case 2: fix_products<2>(re, im, W, S, need); break;
+    case 3: fix_products<3>(re, im, W, S, need); break;
+    case 4: fix_products<4>(re, im, W, S, need); break;
+    case 5: fix_products<5>(re, im, W, S, need); break;
+    case 6: fix_products<6>(re, im, W, S, need); break;
+    case 7: fix_products<7>(re, im, W, S, need); break;
     default: break;
   }
 }
 
 template <typename Idx>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kFixThreads)
     k_expval_fix(const float2 *__restrict__ amp, Idx n_cosets, const FixRunDev run,
                  const FixTermDev *__restrict__ gterms, int S, long long *__restrict__ partials) {
   constexpr int D = kFixD, E = 1 << D, PAIRS = E / 2, NV = kFixTerms + 1;
   __shared__ FixTermDev terms[kFixTerms];
   __shared__ Idx soff[E];
   // per-term accumulators, one column per thread (conflict-free 8-byte rows)
-  __shared__ long long sacc[NV][kThreads];
+  __shared__ long long sacc[NV][kFixThreads];
   const int nt = run.nterms;
   if (threadIdx.x < nt) terms[threadIdx.x] = gterms[threadIdx.x];
   if (threadIdx.x < E) {
@@ -727,7 +736,7 @@ __global__ void __launch_bounds__(kThreads)
       const FixTermDev t = terms[j];
       if (t.u != cur) {
         cur = t.u;
-        fix_dispatch(t.u, re, im, W, S);
+        fix_dispatch(t.u, t.need, re, im, W, S);
       }
       long long sum = 0;
       if (t.u == 0) {
@@ -878,13 +887,18 @@ void plan_fix(const sv_state *sv, const uint64_t *x, const uint64_t *z, const do
         ts.push_back({u, &t});
       }
     std::stable_sort(ts.begin(), ts.end(), [](const auto &a1, const auto &b1) { return a1.first < b1.first; });
+    std::map<int, int> need;
+    for (auto &ut : ts) {
+      const int ny = popc64(ut.second->x & ut.second->z) & 3;
+      need[ut.first] |= ut.first == 0 ? 1 : ((ny & 1) ? 2 : 1);
+    }
     for (auto &ut : ts) {
       const Term &t = *ut.second;
       const int u = ut.first;
       FixTermDev e;
       e.z = t.z;
       e.u = u;
-      e.pad = 0;
+      e.need = need[u];
       uint32_t psm = 0;
       auto sgn = [&](int l) {
         uint64_t so = 0;
@@ -918,10 +932,17 @@ template <typename Idx>
 int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *energy, double *norm2) {
   constexpr int NV = kFixTerms + 1;
   static int cap = 0;
-  if (!cap) cap = occ_blocks(k_expval_fix<Idx>);
+  if (!cap) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expval_fix<Idx>, kFixThreads, 0) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    cap = (per_sm > 0 ? per_sm : 1) * device_sm_count();
+  }
   const uint64_t n_amps = 1ULL << sv->n;
   const uint64_t n_cosets = n_amps >> kFixD;
-  uint64_t need = (n_cosets + kThreads - 1) / kThreads;
+  uint64_t need = (n_cosets + kFixThreads - 1) / kFixThreads;
   const int blocks = (int)(need < (uint64_t)cap ? (need ? need : 1) : cap);
   const int est_blocks = 64;
   // partial sums (int64) and the S estimate share the double scratch
@@ -963,7 +984,7 @@ int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *ener
   long long *res = (long long *)sv->d_results;
   for (size_t r = 0; r < runs.size(); ++r) {
     const int tr = trace_begin(sv);
-    k_expval_fix<Idx><<<blocks, kThreads, 0, sv->stream>>>(
+    k_expval_fix<Idx><<<blocks, kFixThreads, 0, sv->stream>>>(
         (const float2 *)sv->amps, (Idx)n_cosets, runs[r].dev, (const FixTermDev *)((char *)sv->d_stage + off[r]), S,
         part + (size_t)NV * blocks * r);
     PR_CHECK_LAUNCH();
