@@ -317,6 +317,10 @@ def run_ours(a):
                                      "rotations_per_s": g_rate, "speedup": (R / (ms_step / 1000.0)) / g_rate,
                                      "sample": "every 4th rotation of the first Trotter step"}
 
+    # batched independent states: one persistent launch vs one launch per pass per state
+    if not a.skip_extras:
+        extras["batched"] = batch_measure(capi, torch, stream, sh, barrier)
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not a.skip_extras:
@@ -383,6 +387,50 @@ def run_ours(a):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def batch_measure(capi, torch, stream, sh, barrier, reps: int = 3):
+    """64 independent JW-shaped problems, n ~ U{12..22}, complex64, T ~ U{100..800},
+    dt ~ U[0.01, 0.2], 1..8 first-order steps each."""
+    wl = synth.batch_workload(64, seed=4)
+    states, plans, total = [], [], 0
+    for circ in wl:
+        rx, rz, rt = capi.trotter_expand(circ.ham.x, circ.ham.z, circ.ham.c, circ.dt, circ.steps, 1, False)
+        total += len(rt)
+        sv = capi.sv_alloc(circ.n, "c64", sh)
+        capi.sv_set_basis_state(sv, circ.basis_state)
+        states.append(sv)
+        plans.append(capi.plan_create(circ.n, "c64", rx, rz, rt, -1, sh))
+    out = {"states": len(wl), "rotations": total, "n_range": [min(c.n for c in wl), max(c.n for c in wl)]}
+    try:
+        capi.batch_run(states, plans, use_graph=True)  # builds, captures, warms
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            capi.batch_run(states, plans, use_graph=True)
+        barrier()
+        el = (time.perf_counter() - t0) / reps
+        grid, multi, used_graph = capi.batch_info()
+        out.update({"persistent_ms": 1000 * el, "persistent_rotations_per_s": total / el, "grid_ctas": grid,
+                    "multi_cta_states": multi, "graph": bool(used_graph)})
+        for sv, p in zip(states, plans):  # warm the one-launch-per-pass path
+            capi.plan_apply(sv, p)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for sv, p in zip(states, plans):
+                capi.plan_apply(sv, p)
+        barrier()
+        el2 = (time.perf_counter() - t0) / reps
+        launches = sum(capi.plan_stats(p)[1] for p in plans)
+        out.update({"per_state_ms": 1000 * el2, "per_state_rotations_per_s": total / el2,
+                    "per_state_launches": launches, "speedup": el2 / el})
+    finally:
+        for p in plans:
+            capi.plan_free(p)
+        for sv in states:
+            capi.sv_free(sv)
+    return out
 
 
 def main():

@@ -237,6 +237,26 @@ int apply_pauli_rotations_gates(sv_state *sv, const uint64_t *x, const uint64_t 
  * wait that runs out sets an error word and the call returns SV_ETIMEOUT. */
 int batch_run(sv_state **states, sv_plan **plans, size_t count, int use_graph);
 
+/* Options of batch_run_ex. */
+typedef struct sv_batch_opts {
+  double wait_timeout_s; /* limit on each device-side barrier wait, seconds (<= 0: 1.0) */
+  int test_skip_arrival; /* testing only: one CTA of the first state that spans several CTAs
+                            skips its first barrier arrival, so its peers' waits run out and
+                            the call returns SV_ETIMEOUT (the failure path, without a fault) */
+} sv_batch_opts;
+
+/* batch_run with options (opts may be NULL).  Plans must use fusion_depth <= 4.
+ * The work assignment and device buffers are cached for the last (states,
+ * plans) set; with use_graph the launch is captured once into a CUDA graph and
+ * replayed (the state handles' streams must not be the legacy default stream;
+ * if capture is unavailable the launch is issued directly).  Each call
+ * synchronises the stream of states[0] to read the error word. */
+int batch_run_ex(sv_state **states, sv_plan **plans, size_t count, int use_graph, const sv_batch_opts *opts);
+
+/* Shape of the last batched launch: CTAs in the grid, states that spanned
+ * several CTAs, whether a CUDA graph was used. */
+int batch_info(int *grid_ctas, int *multi_cta_states, int *graph_used);
+
 /* ---- tracing (not in the paper) --------------------------------------------------------- */
 
 /* One row per kernel name: launches, summed device time and algorithmic HBM

@@ -86,6 +86,8 @@ def lib() -> ctypes.CDLL:
         "rotation_grads": ([vp, vp, vp, vp, sz, vp, vp, vp, sz, P(d), vp], i),
         "apply_pauli_rotations_gates": ([vp, vp, vp, vp, sz, P(sz)], i),
         "batch_run": ([vp, vp, sz, i], i),
+        "batch_run_ex": ([vp, vp, sz, i, vp], i),
+        "batch_info": ([P(i), P(i), P(i)], i),
         "sv_trace_start": ([vp], i),
         "sv_trace_stop": ([vp, vp, i, P(i)], i),
     }
@@ -103,7 +105,8 @@ def exported_symbols() -> Sequence[str]:
             "sv_materialize", "sv_copy", "frame_reset", "frame_apply_pauli", "frame_get",
             "apply_pauli_rotations", "plan_create", "plan_apply", "plan_free", "plan_stats",
             "trotter_expand", "expval_pauli_sum", "expval_pauli_sum_noalloc", "apply_pauli_sum", "rotation_grads",
-            "apply_pauli_rotations_gates", "batch_run", "sv_trace_start", "sv_trace_stop"]
+            "apply_pauli_rotations_gates", "batch_run", "batch_run_ex", "batch_info", "sv_trace_start",
+            "sv_trace_stop"]
 
 
 def _check(rc: int) -> None:
@@ -292,12 +295,32 @@ def apply_pauli_rotations_gates(sv: int, x, z, angles) -> int:
     return n.value
 
 
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("wait_timeout_s", ctypes.c_double), ("test_skip_arrival", ctypes.c_int)]
+
+
 def batch_run(states: Sequence[int], plans: Sequence[int], use_graph: bool = True) -> None:
     if len(states) != len(plans):
         raise ValueError("states and plans must have equal length")
     sa = (ctypes.c_void_p * len(states))(*states)
     pa = (ctypes.c_void_p * len(plans))(*plans)
     _check(lib().batch_run(sa, pa, len(states), 1 if use_graph else 0))
+
+
+def batch_run_ex(states: Sequence[int], plans: Sequence[int], use_graph: bool = True,
+                 wait_timeout_s: float = 0.0, test_skip_arrival: bool = False) -> None:
+    if len(states) != len(plans):
+        raise ValueError("states and plans must have equal length")
+    sa = (ctypes.c_void_p * len(states))(*states)
+    pa = (ctypes.c_void_p * len(plans))(*plans)
+    opts = BatchOpts(float(wait_timeout_s), 1 if test_skip_arrival else 0)
+    _check(lib().batch_run_ex(sa, pa, len(states), 1 if use_graph else 0, ctypes.byref(opts)))
+
+
+def batch_info() -> Tuple[int, int, int]:
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().batch_info(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
 
 
 class TraceRow(ctypes.Structure):

@@ -191,6 +191,9 @@ int trace_begin(sv_state *sv);
 void trace_end(sv_state *sv, int slot, int name, double bytes);
 void trace_release(sv_state *sv);
 
+// batched launches (batch.cu): forget a cached batch that uses a freed handle
+void batch_forget(const sv_state *sv, const sv_plan *plan);
+
 // device memory helpers (state.cu)
 int ensure_scratch(sv_state *sv, size_t partial_doubles, size_t result_doubles);
 int ensure_stage(sv_state *sv, size_t bytes);
@@ -199,6 +202,7 @@ int device_sm_count();
 // launch one run of a plan (rotate.cu)
 int launch_run(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t fx, uint64_t fz);
 int prepare_tables(int dtype);
+int table_pointer(int dtype, const void **out);
 // in-place frame application (rotate.cu)
 int launch_materialize(sv_state *sv, uint64_t x, uint64_t z, int q);
 int launch_set_basis(sv_state *sv, uint64_t k);

@@ -1,0 +1,537 @@
+// Device code of the rotation passes, shared by the one-pass-per-launch
+// kernels (rotate.cu) and the persistent batched kernel (batch.cu).
+//
+// Every pass is a __device__ body over one CTA's share of the index space
+// (cta_rank of cta_count CTAs) with an explicit shared-memory workspace, so a
+// caller can run passes back to back in one launch.
+#pragma once
+
+#include "internal.h"
+
+namespace pr {
+
+namespace {
+
+template <typename R>
+struct Cx;
+template <>
+struct Cx<float> {
+  using T = float2;
+};
+template <>
+struct Cx<double> {
+  using T = double2;
+};
+
+__device__ __forceinline__ int parity(uint32_t v) { return __popc(v) & 1; }
+__device__ __forceinline__ int parity(uint64_t v) { return __popcll(v) & 1; }
+
+template <typename R, typename Idx>
+struct RotSm {
+  Idx z;
+  uint32_t zt;
+  uint32_t code;
+  R t;
+};
+
+// Apply one rotation with coset coordinates U (compile-time) to V cosets of
+// 2^D elements.  tp[v] is t times the sign (-1)^{popc(rep_v & z)}; bit l of zt
+// adds the sign of coset element l.
+template <int D, int V, int U, int IMAG, typename R, typename C>
+__device__ __forceinline__ void apply_u(C (&a)[V][1 << D], const R (&tp)[V], uint32_t zt) {
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+#pragma unroll
+    for (int l = 0; l < (1 << D); ++l) {
+      if (U == 0) {
+        const R t = ((zt >> l) & 1u) ? -tp[v] : tp[v];
+        const C x = a[v][l];
+        a[v][l].x = x.x - t * x.y;
+        a[v][l].y = x.y + t * x.x;
+      } else if ((l ^ U) > l) {
+        const int m = l ^ U;
+        const R tl = ((zt >> l) & 1u) ? -tp[v] : tp[v];
+        const R tm = IMAG ? tl : -tl;
+        const C al = a[v][l], am = a[v][m];
+        if (IMAG) {
+          a[v][l].x = al.x - tl * am.y;
+          a[v][l].y = al.y + tl * am.x;
+          a[v][m].x = am.x - tm * al.y;
+          a[v][m].y = am.y + tm * al.x;
+        } else {
+          a[v][l].x = al.x + tl * am.x;
+          a[v][l].y = al.y + tl * am.y;
+          a[v][m].x = am.x + tm * al.x;
+          a[v][m].y = am.y + tm * al.y;
+        }
+      }
+    }
+  }
+}
+
+#define PR_CASE(K)                                                                 \
+  case K:                                                                          \
+    if constexpr ((((K) >> 1) < (1 << D)) && ((((K) >> 1) != 0) || ((K)&1)))       \
+      apply_u<D, V, ((K) >> 1), ((K)&1)>(a, tp, zt);                               \
+    break;
+#define PR_CASE8(B) \
+  PR_CASE(B + 0) PR_CASE(B + 1) PR_CASE(B + 2) PR_CASE(B + 3) PR_CASE(B + 4) PR_CASE(B + 5) PR_CASE(B + 6) PR_CASE(B + 7)
+
+template <int D, int V, typename R, typename C>
+__device__ __forceinline__ void dispatch(uint32_t code, C (&a)[V][1 << D], const R (&tp)[V], uint32_t zt) {
+  switch (code) {
+    PR_CASE8(0)
+    PR_CASE8(8)
+    PR_CASE8(16)
+    PR_CASE8(24)
+    PR_CASE8(32)
+    PR_CASE8(40)
+    PR_CASE8(48)
+    PR_CASE8(56)
+    default:
+      break;
+  }
+}
+
+template <typename R, typename Idx, int D>
+__host__ __device__ constexpr size_t ws_coset() {
+  return ((sizeof(RotSm<R, Idx>) * kMaxRunRots + 15) & ~size_t(15)) + sizeof(Idx) * (1u << D);
+}
+
+// One CTA's share of a fused coset run: cosets cta_rank*chunk + t, stepping by
+// cta_count*chunk.  ws: ws_coset<R, Idx, D>() bytes of shared memory.
+template <typename R, typename Idx, int D, int V>
+__device__ __forceinline__ void body_coset(typename Cx<R>::T *__restrict__ amp, Idx n_cosets, const RunDev &run,
+                                           const RotDev *__restrict__ rots, uint64_t fx, uint64_t fz,
+                                           Idx cta_rank, Idx cta_count, char *ws) {
+  using C = typename Cx<R>::T;
+  constexpr int E = 1 << D;
+  RotSm<R, Idx> *srot = (RotSm<R, Idx> *)ws;
+  Idx *soff = (Idx *)(ws + ((sizeof(RotSm<R, Idx>) * kMaxRunRots + 15) & ~size_t(15)));
+  const int count = run.count;
+  for (int j = threadIdx.x; j < count; j += blockDim.x) {
+    const RotDev r = rots[run.first + j];
+    double t = r.t;
+    if (__popcll((r.x & fz) ^ (r.z & fx)) & 1) t = -t;  // runtime frame sign
+    RotSm<R, Idx> s;
+    s.z = (Idx)r.z;
+    s.zt = r.zt;
+    s.code = r.code;
+    s.t = (R)t;
+    srot[j] = s;
+  }
+  if (threadIdx.x < E) {
+    uint64_t s = 0;
+    for (int b = 0; b < D; ++b)
+      if ((threadIdx.x >> b) & 1) s ^= run.basis[b];
+    soff[threadIdx.x] = (Idx)s;
+  }
+  __syncthreads();
+
+  const Idx chunk = (Idx)blockDim.x * V;
+  const Idx stride = cta_count * chunk;
+  for (Idx c0 = cta_rank * chunk + threadIdx.x; c0 < n_cosets; c0 += stride) {
+    C a[V][E];
+    Idx rep[V];
+    bool ok[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const Idx c = c0 + (Idx)(v * blockDim.x);
+      Idx r = c;
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        const int p = run.piv[b];
+        r = ((r >> p) << (p + 1)) | (r & ((Idx(1) << p) - 1));
+      }
+      rep[v] = r;
+      ok[v] = c < n_cosets;
+#pragma unroll
+      for (int l = 0; l < E; ++l) {
+        if (ok[v]) {
+          a[v][l] = amp[r ^ soff[l]];
+        } else {
+          a[v][l].x = 0;
+          a[v][l].y = 0;
+        }
+      }
+    }
+    for (int j = 0; j < count; ++j) {
+      const RotSm<R, Idx> s = srot[j];
+      R tp[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) tp[v] = parity(rep[v] & s.z) ? -s.t : s.t;
+      dispatch<D, V>(s.code, a, tp, s.zt);
+    }
+    if (run.fold) {
+      const R fr = (R)run.fold_re, fi = (R)run.fold_im;
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int l = 0; l < E; ++l) {
+          const C x = a[v][l];
+          a[v][l].x = fr * x.x - fi * x.y;
+          a[v][l].y = fr * x.y + fi * x.x;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+      if (ok[v]) {
+#pragma unroll
+        for (int l = 0; l < E; ++l) amp[rep[v] ^ soff[l]] = a[v][l];
+      }
+  }
+  __syncthreads();  // the workspace may be reused by the caller's next pass
+}
+
+// ------------------------------------------------------------------ complex64, packed pairs
+//
+// k_coset_c64x2: the same fused pass for complex64 with two adjacent cosets
+// per thread (representatives rep and rep|1, bit 0 not a pivot).  Element l of
+// both cosets lies in one aligned 16-byte float4 (its halves swapped when
+// bit 0 of the element offset is set), so each element is one 16-byte load.
+// Registers hold RE[l] = (re of coset 0, re of coset 1) and IM[l] likewise, and
+// every update is a packed FP32x2 fused multiply-add.  The sign of element l
+// for a rotation is (-1)^{popc(rep & z)} * chi(l) with chi a character of l
+// (chi(l) = prod of S_b over the set bits b of l, S_b = (-1)^{popc(basis_b & z)}),
+// so walking the pair leaders in Gray-code order updates the coefficient with one
+// packed multiply by +-1 per pair instead of a per-element select.
+
+// per-rotation values shared by the CTA: tt[p0 | p1 << 1] = (+-t, +-t) for the
+// two coset parities, S[b] = (s_b, s_b) with s_b = (-1)^{popc(basis_b & z)}
+template <typename Idx>
+struct RotSm2 {
+  Idx z;
+  uint32_t code;
+  float2 tt[4];
+  float2 S[4];
+};
+
+// free-bit index k (0-based among bits != H) -> bit position
+template <int H>
+__device__ __host__ constexpr int free_bit(int k) {
+  return k < H ? k : k + 1;
+}
+// Gray code over the D-1 free bits, mapped to element index bits
+template <int D, int H>
+__device__ __host__ constexpr int gray_leader(int i) {
+  int g = i ^ (i >> 1), l = 0;
+  for (int k = 0; k < D - 1; ++k)
+    if ((g >> k) & 1) l |= 1 << free_bit<H>(k);
+  return l;
+}
+__device__ __host__ constexpr int ctz_c(int v) {
+  int c = 0;
+  while (!(v & 1)) {
+    v >>= 1;
+    ++c;
+  }
+  return c;
+}
+__device__ __host__ constexpr int high_bit(int v) {
+  int h = 0;
+  while (v >> (h + 1)) ++h;
+  return h;
+}
+
+// negated coefficient written inline, so the compiler can fold the sign into
+// the packed FMA instead of carrying a second chain
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+
+// Pair update from the old values of both elements (exact tan form; the
+// compiler keeps copies of the old values where a 2-cycle needs them).
+template <int D, int U, int IMAG>
+__device__ __forceinline__ void apply_x2(float2 (&RE)[1 << D], float2 (&IM)[1 << D], float2 T,
+                                         const float2 (&S)[D > 0 ? D : 1]) {
+  if constexpr (U == 0) {
+    // diagonal: every element, Gray order over all D bits
+#pragma unroll
+    for (int i = 0; i < (1 << D); ++i) {
+      if (i > 0) T = __fmul2_rn(T, S[ctz_c(i)]);
+      const int l = i ^ (i >> 1);
+      const float2 re = RE[l], im = IM[l];
+      RE[l] = __ffma2_rn(neg2(T), im, re);
+      IM[l] = __ffma2_rn(T, re, im);
+    }
+  } else {
+    constexpr int H = high_bit(U);
+#pragma unroll
+    for (int i = 0; i < (1 << (D - 1)); ++i) {
+      if (i > 0) T = __fmul2_rn(T, S[free_bit<H>(ctz_c(i))]);
+      const float2 N = neg2(T);
+      const int l = gray_leader<D, H>(i);
+      const int m = l ^ U;
+      const float2 rl = RE[l], il = IM[l], rm = RE[m], im = IM[m];
+      if (IMAG) {
+        RE[l] = __ffma2_rn(N, im, rl);
+        IM[l] = __ffma2_rn(T, rm, il);
+        RE[m] = __ffma2_rn(N, il, rm);
+        IM[m] = __ffma2_rn(T, rl, im);
+      } else {
+        RE[l] = __ffma2_rn(T, rm, rl);
+        IM[l] = __ffma2_rn(T, im, il);
+        RE[m] = __ffma2_rn(N, rl, rm);
+        IM[m] = __ffma2_rn(N, il, im);
+      }
+    }
+  }
+}
+
+#define PR_CASE2(K)                                                                \
+  case K:                                                                          \
+    if constexpr ((((K) >> 1) < (1 << D)) && ((((K) >> 1) != 0) || ((K)&1)))       \
+      apply_x2<D, ((K) >> 1), ((K)&1)>(RE, IM, T, S);                           \
+    break;
+#define PR_CASE2_8(B) \
+  PR_CASE2(B + 0) PR_CASE2(B + 1) PR_CASE2(B + 2) PR_CASE2(B + 3) PR_CASE2(B + 4) PR_CASE2(B + 5) PR_CASE2(B + 6) PR_CASE2(B + 7)
+
+template <int D>
+__device__ __forceinline__ void dispatch_x2(uint32_t code, float2 (&RE)[1 << D], float2 (&IM)[1 << D], float2 T,
+                                            const float2 (&S)[D > 0 ? D : 1]) {
+  switch (code) {
+    PR_CASE2_8(0)
+    PR_CASE2_8(8)
+    PR_CASE2_8(16)
+    PR_CASE2_8(24)
+    default:
+      break;
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename Idx, int D>
+__device__ __forceinline__ Idx pair_rep(Idx c, const RunDev &run) {
+  Idx rep = c << 1;
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    const int p = run.piv[b];
+    rep = ((rep >> p) << (p + 1)) | (rep & ((Idx(1) << p) - 1));
+  }
+  return rep;
+}
+
+template <typename Idx, int D>
+__host__ __device__ constexpr size_t ws_c64x2_head() {
+  return ((sizeof(RotSm2<Idx>) * kMaxRunRots + sizeof(Idx) * (1u << D)) + 15) & ~size_t(15);
+}
+// workspace: rotation table, element offsets, then one 16-byte slot per element
+// per thread laid out [element][thread] so a warp's accesses to one element
+// are contiguous
+template <typename Idx, int D>
+__host__ __device__ constexpr size_t ws_c64x2() {
+  return ws_c64x2_head<Idx, D>() + sizeof(float4) * kThreads * (1u << D);
+}
+
+template <typename Idx, int D>
+__device__ __forceinline__ void body_c64x2(float4 *__restrict__ amp4, Idx n_pairs, const RunDev &run,
+                                           const RotDev *__restrict__ rots, uint64_t fx, uint64_t fz,
+                                           Idx cta_rank, Idx cta_count, char *ws) {
+  constexpr int E = 1 << D;
+  RotSm2<Idx> *srot = (RotSm2<Idx> *)ws;
+  Idx *soff = (Idx *)(ws + sizeof(RotSm2<Idx>) * kMaxRunRots);
+  float4 *stage = (float4 *)(ws + ws_c64x2_head<Idx, D>());
+  const int count = run.count;
+  for (int j = threadIdx.x; j < count; j += blockDim.x) {
+    const RotDev r = rots[run.first + j];
+    double t = r.t;
+    if (__popcll((r.x & fz) ^ (r.z & fx)) & 1) t = -t;  // runtime frame sign
+    const float tf = (float)t;
+    RotSm2<Idx> s;
+    s.z = (Idx)r.z;
+    s.code = r.code;
+    s.tt[0] = make_float2(tf, tf);
+    s.tt[1] = make_float2(-tf, tf);
+    s.tt[2] = make_float2(tf, -tf);
+    s.tt[3] = make_float2(-tf, -tf);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float sb = (b < D && ((r.zt >> (1 << b)) & 1u)) ? -1.0f : 1.0f;
+      s.S[b] = make_float2(sb, sb);
+    }
+    srot[j] = s;
+  }
+  if (threadIdx.x < E) {
+    uint64_t s = 0;
+    for (int b = 0; b < D; ++b)
+      if ((threadIdx.x >> b) & 1) s ^= run.basis[b];
+    soff[threadIdx.x] = (Idx)s;
+  }
+  __syncthreads();
+
+  const Idx stride = cta_count * blockDim.x;
+  float4 *slot = stage + threadIdx.x;
+  Idx c = cta_rank * blockDim.x + threadIdx.x;
+  // prefetch the first coset pair
+  if (c < n_pairs) {
+    const Idx rep0 = pair_rep<Idx, D>(c, run);
+#pragma unroll
+    for (int l = 0; l < E; ++l) cp_async16(slot + l * blockDim.x, amp4 + ((rep0 ^ soff[l]) >> 1));
+    cp_async_commit();
+  }
+  for (; c < n_pairs; c += stride) {
+    const Idx rep = pair_rep<Idx, D>(c, run);
+    cp_async_wait_all();
+    float2 RE[E], IM[E];
+#pragma unroll
+    for (int l = 0; l < E; ++l) {
+      const Idx e = rep ^ soff[l];
+      const float4 v = slot[l * blockDim.x];
+      if (e & 1) {
+        RE[l] = make_float2(v.z, v.x);
+        IM[l] = make_float2(v.w, v.y);
+      } else {
+        RE[l] = make_float2(v.x, v.z);
+        IM[l] = make_float2(v.y, v.w);
+      }
+    }
+    // the slot is free again: prefetch the next coset pair while this one computes
+    const Idx cn = c + stride;
+    if (cn < n_pairs) {
+      const Idx repn = pair_rep<Idx, D>(cn, run);
+#pragma unroll
+      for (int l = 0; l < E; ++l) cp_async16(slot + l * blockDim.x, amp4 + ((repn ^ soff[l]) >> 1));
+      cp_async_commit();
+    }
+    for (int j = 0; j < count; ++j) {
+      const RotSm2<Idx> &s = srot[j];
+      const Idx z = s.z;
+      const int p0 = parity(rep & z);
+      const int q = p0 | ((p0 ^ (int)(z & 1)) << 1);
+      const float2 T = s.tt[q];
+      float2 S[D > 0 ? D : 1];
+#pragma unroll
+      for (int b = 0; b < (D > 0 ? D : 1); ++b) S[b] = s.S[b];
+      dispatch_x2<D>(s.code, RE, IM, T, S);
+    }
+    if (run.fold) {
+      const float fr = (float)run.fold_re, fi = (float)run.fold_im;
+      const float2 FR = make_float2(fr, fr), FI = make_float2(fi, fi), NFI = make_float2(-fi, -fi);
+#pragma unroll
+      for (int l = 0; l < E; ++l) {
+        const float2 re = RE[l], im = IM[l];
+        RE[l] = __ffma2_rn(NFI, im, __fmul2_rn(FR, re));
+        IM[l] = __ffma2_rn(FI, re, __fmul2_rn(FR, im));
+      }
+    }
+    // recompute the element addresses instead of keeping 2^D of them live
+    // across the rotation loop
+    asm volatile("" ::: "memory");
+#pragma unroll
+    for (int l = 0; l < E; ++l) {
+      const Idx e = rep ^ soff[l];
+      float4 v;
+      if (e & 1)
+        v = make_float4(RE[l].y, IM[l].y, RE[l].x, IM[l].x);
+      else
+        v = make_float4(RE[l].x, IM[l].x, RE[l].y, IM[l].y);
+      amp4[e >> 1] = v;
+    }
+  }
+  __syncthreads();  // the workspace may be reused by the caller's next pass
+}
+
+// ------------------------------------------------------------------ diagonal phase sums
+
+constexpr int kCls = 1 << kDiagClassBits;  // 16 amplitudes per thread
+
+template <typename R>
+__device__ __forceinline__ typename Cx<R>::T cmul(typename Cx<R>::T a, typename Cx<R>::T b) {
+  typename Cx<R>::T o;
+  o.x = a.x * b.x - a.y * b.y;
+  o.y = a.x * b.y + a.y * b.x;
+  return o;
+}
+
+// e^{i 2 pi phi / 2^64}
+template <typename R>
+__device__ __forceinline__ typename Cx<R>::T turn_phase(uint64_t phi, const typename Cx<R>::T *tab) {
+  using C = typename Cx<R>::T;
+  const C t0 = tab[phi >> 56];
+  const C t1 = tab[256 + ((phi >> 48) & 255u)];
+  const uint64_t rem = phi & ((1ULL << 48) - 1ULL);
+  C s;
+  if (sizeof(R) == 8) {
+    const double x = (double)rem * 3.4061215800865545e-19;  // 2 pi / 2^64
+    const double x2 = x * x;
+    s.x = (R)fma(-0.5, x2, 1.0);
+    s.y = (R)fma(x2 * (-1.0 / 6.0), x, x);
+  } else {
+    // top 32 of the 48 residual bits: a 32-bit conversion (the 64-bit one runs
+    // on the FP64 pipe) is exact enough for float
+    const float x = (float)(uint32_t)(rem >> 16) * 2.23223584e-14f;  // 2 pi / 2^48
+    s.x = fmaf(-0.5f * x, x, 1.0f);
+    s.y = x;
+  }
+  return cmul<R>(cmul<R>(t0, t1), s);
+}
+
+template <typename R, typename Idx>
+__host__ __device__ constexpr size_t ws_diag() {
+  return sizeof(uint64_t) * kMaxDiagRots + sizeof(Idx) * kMaxDiagRots + sizeof(typename Cx<R>::T) * 512;
+}
+
+template <typename R, typename Idx>
+__device__ __forceinline__ void body_diag(typename Cx<R>::T *__restrict__ amp, Idx n_groups, const RunDev &run,
+                                          const DiagDev *__restrict__ rots, uint64_t fx,
+                                          const typename Cx<R>::T *__restrict__ tab, Idx cta_rank, Idx cta_count,
+                                          char *ws) {
+  using C = typename Cx<R>::T;
+  uint64_t *sa = (uint64_t *)ws;
+  C *stab = (C *)(ws + sizeof(uint64_t) * kMaxDiagRots);
+  Idx *sz = (Idx *)(ws + sizeof(uint64_t) * kMaxDiagRots + sizeof(C) * 512);
+  const int count = run.count;
+  for (int j = threadIdx.x; j < count; j += blockDim.x) {
+    const DiagDev r = rots[run.first + j];
+    sz[j] = (Idx)r.z;
+    sa[j] = (__popcll(r.z & fx) & 1) ? (0ULL - r.a) : r.a;  // runtime frame sign
+  }
+  for (int j = threadIdx.x; j < 512; j += blockDim.x) stab[j] = tab[j];
+  __syncthreads();
+  const Idx stride = cta_count * blockDim.x;
+  for (Idx g = cta_rank * blockDim.x + threadIdx.x; g < n_groups; g += stride) {
+    const Idx base = (g & (Idx)((1u << kDiagClassLo) - 1u)) |
+                     ((g >> kDiagClassLo) << (kDiagClassLo + kDiagClassBits));
+    uint64_t acc[kCls];
+#pragma unroll
+    for (int c = 0; c < kCls; ++c) {
+      uint64_t s = 0;
+      const int j1 = run.seg[c + 1];
+      for (int j = run.seg[c]; j < j1; ++j) {
+        const uint64_t a = sa[j];
+        s += parity(base & sz[j]) ? (0ULL - a) : a;
+      }
+      acc[c] = s;
+    }
+    // acc[e] <- sum_c (-1)^{popc(e & c)} acc[c]
+#pragma unroll
+    for (int h = 1; h < kCls; h <<= 1)
+#pragma unroll
+      for (int i = 0; i < kCls; ++i)
+        if (!(i & h)) {
+          const uint64_t u = acc[i], w = acc[i + h];
+          acc[i] = u + w;
+          acc[i + h] = u - w;
+        }
+#pragma unroll
+    for (int e = 0; e < kCls; ++e) {
+      const Idx k = base | ((Idx)e << kDiagClassLo);
+      C ph = turn_phase<R>(0ULL - acc[e], stab);  // exp(-i sum_j s_j theta_j / 2)
+      if (run.fold) {
+        C f;
+        f.x = (R)run.fold_re;
+        f.y = (R)run.fold_im;
+        ph = cmul<R>(ph, f);
+      }
+      amp[k] = cmul<R>(amp[k], ph);
+    }
+  }
+  __syncthreads();  // the workspace may be reused by the caller's next pass
+}
+
+}  // namespace
+}  // namespace pr

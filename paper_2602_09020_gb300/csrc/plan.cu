@@ -407,6 +407,7 @@ int plan_apply(sv_state *sv, sv_plan *plan) { return apply_plan(sv, plan); }
 
 int plan_free(sv_plan *plan) {
   if (!plan) return SV_OK;
+  batch_forget(nullptr, plan);
   cudaDeviceSynchronize();
   if (plan->d_rots) cudaFree(plan->d_rots);
   if (plan->d_diag) cudaFree(plan->d_diag);

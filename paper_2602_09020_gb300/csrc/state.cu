@@ -270,6 +270,7 @@ int sv_wrap(sv_state **out, void *dev_amps, int n_qubits, int dtype, void *cuda_
 
 int sv_free(sv_state *sv) {
   if (!sv) return SV_OK;
+  batch_forget(sv, nullptr);
   if (sv->stream) cudaStreamSynchronize(sv->stream);
   else cudaDeviceSynchronize();
   if (sv->owns && sv->amps) cudaFree(sv->amps);
