@@ -412,7 +412,7 @@ def batch_measure(capi, torch, stream, sh, barrier, reps: int = 3):
         el = (time.perf_counter() - t0) / reps
         grid, multi, used_graph = capi.batch_info()
         out.update({"persistent_ms": 1000 * el, "persistent_rotations_per_s": total / el, "grid_ctas": grid,
-                    "multi_cta_states": multi, "graph": bool(used_graph)})
+                    "multi_cta_states": multi, "graph_mode": used_graph})
         for sv, p in zip(states, plans):  # warm the one-launch-per-pass path
             capi.plan_apply(sv, p)
         barrier()

@@ -254,7 +254,10 @@ typedef struct sv_batch_opts {
 int batch_run_ex(sv_state **states, sv_plan **plans, size_t count, int use_graph, const sv_batch_opts *opts);
 
 /* Shape of the last batched launch: CTAs in the grid, states that spanned
- * several CTAs, whether a CUDA graph was used. */
+ * several CTAs, and how it was launched: 1 = cooperative launch replayed from a
+ * CUDA graph, 2 = plain launch of the same grid replayed from a graph, 0 = no
+ * graph, negative = graph capture failed with that cudaError_t (launched
+ * directly instead). */
 int batch_info(int *grid_ctas, int *multi_cta_states, int *graph_used);
 
 /* ---- tracing (not in the paper) --------------------------------------------------------- */
