@@ -1,0 +1,152 @@
+"""Parity at the full sizes of the measured workloads, in the launch
+configuration bench.py times (plans with the default fusion depth).
+
+* n = 24, 2000 terms, 10 first-order steps (20,000 rotations): complex128
+  against oracle amplitudes, norm and <H> stored by tests/golden/make_full_size.py;
+  complex64 infidelity <= 1e-5 against the GPU complex128 run.
+* n = 29 / 30, 5000 terms, 4 second-order steps (one plan per step, 9,999
+  merged rotations each), FP64 norm and <H> after every step: complex64
+  against complex128 at n = 29 (infidelity, |dE|), and the complex64 norm drift
+  at n = 30.
+* n = 20 adjoint workload (500 rotations, angles U[-pi, pi], 300-term
+  observable): all 500 gradients against central differences (h = 1e-4, FP64)
+  and the same generator at n = 10 against the oracle's parameter-shift rule.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2602_09020_gb300 import capi, synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "full_n24_trotter.json")
+
+
+def _torch_state(n, dtype, stream):
+    t = torch.zeros(1 << n, dtype=torch.complex128 if dtype == "c128" else torch.complex64, device="cuda")
+    h = capi.sv_wrap(t.data_ptr(), n, dtype, stream)
+    return t, h
+
+
+def _infidelity(ref, got):
+    r = ref.to(torch.complex128)
+    g = got.to(torch.complex128)
+    ov = torch.vdot(r, g)
+    return float(1.0 - (ov.abs() ** 2) / (torch.vdot(r, r).real * torch.vdot(g, g).real))
+
+
+def _evolve_n24(dtype, stream):
+    ham = synth.jw_hamiltonian(24, 2000, 1)
+    rx, rz, rt = capi.trotter_expand(ham.x, ham.z, ham.c, 0.05, 10, 1, False)
+    t, h = _torch_state(24, dtype, stream)
+    capi.sv_set_basis_state(h, synth.hartree_fock_index(12))
+    p = capi.plan_create(24, dtype, rx, rz, rt, -1, stream)
+    capi.plan_apply(h, p)
+    e, nrm = capi.expval_pauli_sum(h, ham.x, ham.z, ham.c)
+    capi.sv_materialize(h)
+    torch.cuda.synchronize()
+    capi.plan_free(p)
+    capi.sv_free(h)
+    return t, e, nrm
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN), reason="oracle values not generated")
+def test_n24_trotter_against_oracle_and_c64_infidelity():
+    with open(GOLDEN) as fh:
+        gold = json.load(fh)
+    stream = torch.cuda.current_stream().cuda_stream
+    t128, e128, n128 = _evolve_n24("c128", stream)
+    idx = torch.tensor(gold["indices"], device="cuda")
+    got = t128[idx].cpu().numpy()
+    want = np.array(gold["re"]) + 1j * np.array(gold["im"])
+    assert np.max(np.abs(got - want)) <= 1e-12
+    assert abs(n128 - gold["norm2"]) <= 1e-12
+    assert abs(e128 - gold["energy"]) <= 1e-9
+    t64, e64, n64 = _evolve_n24("c64", stream)
+    inf = _infidelity(t128, t64)
+    assert inf <= 1e-5, inf
+    assert abs(e64 - e128) <= 1e-4 and abs(n64 - 1.0) <= 1e-4
+
+
+def test_n29_second_order_c64_vs_c128_and_n30_norm():
+    stream = torch.cuda.current_stream().cuda_stream
+    hams = {29: synth.jw_hamiltonian(29, 5000, 1), 30: synth.jw_hamiltonian(30, 5000, 1)}
+    out = {}
+    for n, dtype in ((29, "c128"), (29, "c64"), (30, "c64")):
+        hx, hz, hc = hams[n].x, hams[n].z, hams[n].c
+        rx, rz, rt = capi.trotter_expand(hx, hz, hc, 0.05, 1, 2, True)
+        t, h = _torch_state(n, dtype, stream)
+        capi.sv_set_basis_state(h, synth.hartree_fock_index(n // 2))
+        p = capi.plan_create(n, dtype, rx, rz, rt, -1, stream)
+        es, ns = [], []
+        for _ in range(4):
+            capi.plan_apply(h, p)
+            e, nrm = capi.expval_pauli_sum(h, hx, hz, hc)
+            es.append(e)
+            ns.append(nrm)
+        capi.sv_materialize(h)
+        torch.cuda.synchronize()
+        capi.plan_free(p)
+        capi.sv_free(h)
+        out[(n, dtype)] = (t, es, ns)
+    t128, e128, n128 = out[(29, "c128")]
+    t64, e64, n64 = out[(29, "c64")]
+    assert max(abs(v - 1.0) for v in n128) <= 1e-12
+    inf = _infidelity(t128, t64)
+    assert inf <= 1e-5, inf
+    assert max(abs(a - b) for a, b in zip(e128, e64)) <= 1e-3 * max(1.0, abs(e128[-1]))
+    _, _, n30 = out[(30, "c64")]
+    assert max(abs(v - 1.0) for v in n30) <= 1e-4
+    del t128, t64
+    torch.cuda.empty_cache()
+
+
+def _energy(n, dtype, psi0_basis, x, z, th, obs, stream):
+    h = capi.sv_alloc(n, dtype, stream)
+    capi.sv_set_basis_state(h, psi0_basis)
+    capi.apply_pauli_rotations(h, x, z, th)
+    e, _ = capi.expval_pauli_sum(h, obs.x, obs.z, obs.c)
+    capi.sv_free(h)
+    return e
+
+
+def test_n20_adjoint_against_central_differences():
+    stream = torch.cuda.current_stream().cuda_stream
+    n = 20
+    x, z, th, obs = synth.adjoint_workload(n, 500, 300, seed=20)
+    basis = synth.hartree_fock_index(n // 2)
+    h = capi.sv_alloc(n, "c128", stream)
+    capi.sv_set_basis_state(h, basis)
+    e, g = capi.rotation_grads(h, x, z, th, obs.x, obs.z, obs.c)
+    capi.sv_free(h)
+    assert abs(e - _energy(n, "c128", basis, x, z, th, obs, stream)) <= 1e-11
+    hstep = 1e-4
+    fd = np.empty(len(th))
+    for j in range(len(th)):
+        tp = th.copy(); tp[j] += hstep
+        tm = th.copy(); tm[j] -= hstep
+        fd[j] = (_energy(n, "c128", basis, x, z, tp, obs, stream) -
+                 _energy(n, "c128", basis, x, z, tm, obs, stream)) / (2 * hstep)
+    assert np.max(np.abs(g - fd)) <= 1e-6 * max(1.0, np.abs(g).max())
+    h = capi.sv_alloc(n, "c64", stream)
+    capi.sv_set_basis_state(h, basis)
+    e32, g32 = capi.rotation_grads(h, x, z, th, obs.x, obs.z, obs.c)
+    capi.sv_free(h)
+    assert np.max(np.abs(g32 - g)) <= 1e-4 * max(1.0, np.abs(g).max())
+
+
+def test_n10_copy_of_adjoint_workload_against_oracle(orc):
+    n = 10
+    x, z, th, obs = synth.adjoint_workload(n, 500, 300, seed=20)
+    basis = synth.hartree_fock_index(n // 2)
+    e_ref, g_ref = orc.grad_param_shift(n, orc.basis_state(n, basis), x, z, th, obs.x, obs.z, obs.c)
+    stream = torch.cuda.current_stream().cuda_stream
+    h = capi.sv_alloc(n, "c128", stream)
+    capi.sv_set_basis_state(h, basis)
+    e, g = capi.rotation_grads(h, x, z, th, obs.x, obs.z, obs.c)
+    capi.sv_free(h)
+    assert abs(e - e_ref) <= 1e-11
+    assert np.max(np.abs(g - g_ref)) <= 1e-10 * max(1.0, np.abs(g_ref).max())
