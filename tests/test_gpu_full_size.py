@@ -63,7 +63,11 @@ def test_n24_trotter_against_oracle_and_c64_infidelity():
     got = t128[idx].cpu().numpy()
     want = np.array(gold["re"]) + 1j * np.array(gold["im"])
     assert np.max(np.abs(got - want)) <= 1e-12
-    assert abs(n128 - gold["norm2"]) <= 1e-12
+    # the exact evolution is unitary: the GPU norm must be 1 to FP64 accuracy.  The
+    # oracle's own norm has drifted by ~2.6e-11: each of its ~160k Hadamard passes
+    # rescales by 2 fl(1/sqrt2)^2 != 1, so its <H> carries a ~1e-10 rounding error
+    assert abs(n128 - 1.0) <= 1e-12
+    assert abs(gold["norm2"] - 1.0) <= 1e-10
     assert abs(e128 - gold["energy"]) <= 1e-9
     t64, e64, n64 = _evolve_n24("c64", stream)
     inf = _infidelity(t128, t64)
