@@ -268,7 +268,8 @@ typedef struct sv_trace_row {
   char name[40];
   int64_t launches;
   double total_ms;
-  double bytes;
+  double bytes; /* algorithmic HBM bytes, summed over launches */
+  double flops; /* algorithmic floating-point operations (FMA = 2), summed */
 } sv_trace_row;
 
 /* Start recording a CUDA event pair around every kernel this handle launches

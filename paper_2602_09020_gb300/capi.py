@@ -325,7 +325,7 @@ def batch_info() -> Tuple[int, int, int]:
 
 class TraceRow(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64),
-                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
 def sv_trace_start(sv: int) -> None:
@@ -333,9 +333,9 @@ def sv_trace_start(sv: int) -> None:
 
 
 def sv_trace_stop(sv: int) -> dict:
-    """Returns {kernel name: (launches, total_ms, algorithmic_bytes)}."""
+    """Returns {kernel name: (launches, total_ms, algorithmic_bytes, algorithmic_flops)}."""
     rows = (TraceRow * 64)()
     n = ctypes.c_int()
     _check(lib().sv_trace_stop(sv, rows, 64, ctypes.byref(n)))
-    return {rows[i].name.decode(): (int(rows[i].launches), float(rows[i].total_ms), float(rows[i].bytes))
-            for i in range(n.value)}
+    return {rows[i].name.decode(): (int(rows[i].launches), float(rows[i].total_ms), float(rows[i].bytes),
+                                    float(rows[i].flops)) for i in range(n.value)}

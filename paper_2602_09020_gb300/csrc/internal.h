@@ -131,6 +131,7 @@ namespace pr {
 struct TraceRec {
   int name;       // index into the kernel name table (trace.cu)
   double bytes;   // algorithmic bytes of this launch
+  double flops;   // algorithmic floating-point operations of this launch
   int ev0, ev1;   // event pool slots
 };
 // kernel name ids for tracing
@@ -188,7 +189,7 @@ struct sv_plan {
 namespace pr {
 // tracing (trace.cu): call trace_begin before a launch and trace_end after it
 int trace_begin(sv_state *sv);
-void trace_end(sv_state *sv, int slot, int name, double bytes);
+void trace_end(sv_state *sv, int slot, int name, double bytes, double flops = 0.0);
 void trace_release(sv_state *sv);
 
 // batched launches (batch.cu): forget a cached batch that uses a freed handle

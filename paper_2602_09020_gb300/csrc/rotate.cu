@@ -79,7 +79,8 @@ int launch_coset_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_
   k_coset<R, Idx, D, V><<<blocks, kThreads, 0, sv->stream>>>((C *)sv->amps, (Idx)n_cosets, run,
                                                              plan->d_rots, fx, fz);
   PR_CHECK_LAUNCH();
-  trace_end(sv, tr, KN_COSET0 + D, 2.0 * (double)sizeof(C) * (double)(1ULL << sv->n));
+  trace_end(sv, tr, KN_COSET0 + D, 2.0 * (double)sizeof(C) * (double)(1ULL << sv->n),
+            4.0 * (double)run.count * (double)(1ULL << sv->n));
   return SV_OK;
 }
 
@@ -104,7 +105,8 @@ int launch_c64x2_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_
   k_coset_c64x2<Idx, D><<<blocks, kThreads, dyn, sv->stream>>>((float4 *)sv->amps, (Idx)n_pairs, run,
                                                                plan->d_rots, fx, fz);
   PR_CHECK_LAUNCH();
-  trace_end(sv, tr, KN_COSET0 + D, 2.0 * 8.0 * (double)(1ULL << sv->n));
+  trace_end(sv, tr, KN_COSET0 + D, 2.0 * 8.0 * (double)(1ULL << sv->n),
+            4.0 * (double)run.count * (double)(1ULL << sv->n));
   return SV_OK;
 }
 

@@ -30,12 +30,12 @@ int trace_begin(sv_state *sv) {
   return s;
 }
 
-void trace_end(sv_state *sv, int slot, int name, double bytes) {
+void trace_end(sv_state *sv, int slot, int name, double bytes, double flops) {
   if (!sv || !sv->tracing || slot < 0) return;
   int e = next_event(sv);
   if (e < 0) return;
   cudaEventRecord(sv->events[e], sv->stream);
-  sv->trace.push_back(TraceRec{name, bytes, slot, e});
+  sv->trace.push_back(TraceRec{name, bytes, flops, slot, e});
 }
 
 void trace_release(sv_state *sv) {
@@ -65,12 +65,14 @@ int sv_trace_stop(sv_state *sv, sv_trace_row *rows, int cap, int *n_rows) {
   PR_CUDA(cudaStreamSynchronize(sv->stream));
   double ms[KN_COUNT] = {0};
   double by[KN_COUNT] = {0};
+  double fl[KN_COUNT] = {0};
   int64_t cnt[KN_COUNT] = {0};
   for (const TraceRec &r : sv->trace) {
     float t = 0.f;
     PR_CUDA(cudaEventElapsedTime(&t, sv->events[r.ev0], sv->events[r.ev1]));
     ms[r.name] += t;
     by[r.name] += r.bytes;
+    fl[r.name] += r.flops;
     cnt[r.name] += 1;
   }
   int w = 0;
@@ -82,6 +84,7 @@ int sv_trace_stop(sv_state *sv, sv_trace_row *rows, int cap, int *n_rows) {
       rows[w].launches = cnt[k];
       rows[w].total_ms = ms[k];
       rows[w].bytes = by[k];
+      rows[w].flops = fl[k];
     }
     ++w;
   }
