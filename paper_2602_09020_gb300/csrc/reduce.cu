@@ -586,37 +586,57 @@ int prepare(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c,
 // ------------------------------------------------------------------ complex64: exact fixed-point sums
 //
 // For complex64 amplitudes every product of two components is an exact 48-bit
-// integer times a power of two.  k_expval_fix rounds each product once to the
-// fixed-point grid 2^-S (S = 60 for a normalised state) and sums the integers
-// exactly, per Pauli term, in 64-bit registers; the FP64 coefficients c_j are
-// applied to the exact per-term sums on the host.  Each sum is therefore exact
-// up to 2^-(S+1) per product -- at least as accurate as accumulating the exact
-// products in FP64 -- and independent of summation order.  It runs on the
-// integer pipes instead of GB300's narrow FP64 pipe.  Cosets of a 3-dimensional
-// x-span hold 8 amplitudes per thread; a run carries at most 16 terms.
+// integer times a power of two.  Each product is rounded once to the
+// fixed-point grid 2^-S (S = 60 for a normalised state); every sum after that
+// is exact 64-bit integer arithmetic.  A per-term sum is therefore exact up to
+// 2^-(S+1) per product -- at least as accurate as accumulating the exact
+// products in FP64 -- and independent of summation order.  The FP64
+// coefficients c_j multiply the exact per-term sums on the host.  All of it
+// runs on the integer pipes instead of GB300's narrow FP64 pipe.
+//
+// Work split.  Terms are grouped by x-mask (Sec. 3: P|k> pairs k with k^x).
+// A thread owns a tile: the coset rep + span(b_0..b_3) of 16 amplitudes,
+// where the basis spans the x-masks of the run and is padded with free index
+// bits.  For an x-mask with coordinates u != 0 in that basis, l and l^u pair
+// up (the leader l has bit H = msb(u) clear), and with zeta_b = parity(b_b & z)
+//   sum_l (-1)^{zeta.l} conj(a_{l^u}) a_l
+//       = 2 sum_leaders (-1)^{zeta.l} Re(conj(a_l) a_m)      nY even
+//       = -2i sum_leaders (-1)^{zeta.l} Im(conj(a_l) a_m)    nY odd,  m = l^u.
+// The 8 pair values W[p] of one (u, part) group go through an in-register
+// Walsh-Hadamard transform; afterwards every term of the group, whatever its
+// z, is one transform entry (zeta with bit H removed) times the tile sign
+// (-1)^{popc(rep & z)}.  u = 0 (diagonal terms, identities and the norm)
+// transforms the 16 values |a_l|^2 instead.  The products and the transform
+// are paid once per group and tile; each term then costs one shared-memory
+// read and one 64-bit add per tile.
 
-constexpr int kFixD = 3;
-constexpr int kFixTerms = 32;
-constexpr int kFixThreads = 128;
+constexpr int kWD = 4;  // tile dimension
+constexpr int kWE = 1 << kWD;
+constexpr int kWTerms = 28;   // terms per run, the norm included
+constexpr int kWGroups = 16;  // (u, part) groups per run
+constexpr int kWThreads = 128;
 
-struct FixTermDev {
-  uint64_t z;
-  uint32_t psm;  // sign bit per pair slot (or per element for u = 0)
-  int32_t u;
-  int32_t imag;
-  int32_t need;  // parts of conj(a_l) a_m any term of this u needs: 1 = Re, 2 = Im
+struct WhtGroupDev {
+  int32_t u;     // coordinates of the x-mask in the run basis
+  int32_t imag;  // u != 0: 0 = Re conj(a_l) a_m, 1 = Im
+  int32_t t0;    // terms [t0, t1) of the run
+  int32_t t1;
 };
-struct FixRunDev {
-  uint64_t basis[kFixD];
-  int32_t piv[kFixD];
-  int32_t d;
+struct WhtTermDev {
+  uint64_t z;
+  int32_t slot;  // transform entry: zeta, with bit msb(u) removed when u != 0
+  int32_t pad;
+};
+struct WhtRunDev {
+  uint64_t basis[kWD];
+  int32_t piv[kWD];  // ascending
+  int32_t ngroups;
   int32_t nterms;
-  int32_t with_norm;
 };
 
 struct FixComp {
-  int32_t m;  // signed integer mantissa, |m| < 2^24
-  int32_t e;  // value = m * 2^e
+  int32_t m;  // signed mantissa times 2^7: |m| < 2^31, low 7 bits clear
+  int32_t e;  // value = m * 2^(e - 7)
 };
 
 __device__ __forceinline__ FixComp fix_split(float f) {
@@ -624,20 +644,24 @@ __device__ __forceinline__ FixComp fix_split(float f) {
   const int32_t ex = (int32_t)((b >> 23) & 0xffu);
   int32_t m = (int32_t)(b & 0x7fffffu);
   if (ex) m |= 0x800000;
+  m <<= 7;
   FixComp c;
   c.m = (b >> 31) ? -m : m;
   c.e = (ex ? ex : 1) - 150;
   return c;
 }
 
-// round(a * b * 2^S).  The caller picks S so that every component satisfies
-// |x| <= 2^((60 - S)/2) (S = 60 - ceil(log2 <a|a>)), hence a.e + b.e + S <= 14
-// and the shift k below is never negative: one rounding right shift of the
-// exact 48-bit product pre-shifted by 14 (|p| < 2^48, so p << 14 < 2^62).
-__device__ __forceinline__ long long fix_mul(FixComp a, FixComp b, int S) {
-  const long long p = (long long)a.m * (long long)b.m;
-  const int k = min(max(14 - (a.e + b.e + S), 0), 63);
-  return ((p << 14) + ((1LL << k) >> 1)) >> k;
+// round(a * b * 2^S) with K = 14 - S.  The caller picks S so that every
+// component satisfies |x| <= 2^((60 - S)/2) (S = 60 - ceil(log2 <a|a>)), hence
+// a.e + b.e + S <= 14 and the shift k is never negative.  The product
+// m_a m_b 2^14 is exact (|.| < 2^62); adding half a unit before the
+// arithmetic right shift rounds to nearest.  k is capped at 63: there the
+// added 2^62 makes every p (|p| < 2^62) non-negative and below 2^63, so the
+// result is 0, the correctly rounded value of a product below half a unit.
+__device__ __forceinline__ long long fix_mul(FixComp a, FixComp b, int K) {
+  const int k = min(K - a.e - b.e, 63);
+  const long long half = (1LL << k) >> 1;
+  return ((long long)a.m * (long long)b.m + half) >> k;
 }
 
 __host__ __device__ constexpr int fix_high_bit(int v) {
@@ -650,129 +674,153 @@ __host__ __device__ constexpr int fix_leader(int p, int H) {
   return ((p >> H) << (H + 1)) | (p & ((1 << H) - 1));
 }
 
-template <int U>
-__device__ __forceinline__ void fix_products(const FixComp (&re)[1 << kFixD], const FixComp (&im)[1 << kFixD],
-                                             long long (&W)[1 << kFixD], int S, int need) {
-  constexpr int E = 1 << kFixD, PAIRS = E / 2;
-  if (U == 0) {
+// in-place transform W^[i] = sum_p (-1)^{popc(p & i)} W[p] over N = 2^d entries
+template <int N>
+__device__ __forceinline__ void fix_wht(long long (&W)[kWE]) {
+  constexpr int LOG = fix_high_bit(N);
 #pragma unroll
-    for (int l = 0; l < E; ++l) W[l] = fix_mul(re[l], re[l], S) + fix_mul(im[l], im[l], S);
-  } else {
-    constexpr int H = fix_high_bit(U);
-    if (need & 1) {
+  for (int lv = 0; lv < LOG; ++lv) {
+    const int h = 1 << lv;
 #pragma unroll
-      for (int p = 0; p < PAIRS; ++p) {
-        const int l = fix_leader(p, H), m = l ^ U;
-        W[p] = fix_mul(re[l], re[m], S) + fix_mul(im[l], im[m], S);  // Re conj(a_l) a_m
+    for (int p = 0; p < N; ++p)
+      if (!(p & h)) {
+        const long long a = W[p], b = W[p | h];
+        W[p] = a + b;
+        W[p | h] = a - b;
       }
-    }
-    if (need & 2) {
-#pragma unroll
-      for (int p = 0; p < PAIRS; ++p) {
-        const int l = fix_leader(p, H), m = l ^ U;
-        W[PAIRS + p] = fix_mul(re[l], im[m], S) - fix_mul(im[l], re[m], S);  // Im conj(a_l) a_m
-      }
-    }
   }
 }
 
-__device__ __forceinline__ void fix_dispatch(int u, int need, const FixComp (&re)[1 << kFixD],
-                                             const FixComp (&im)[1 << kFixD], long long (&W)[1 << kFixD], int S) {
+// products and transform of one group; the N entries go to the thread's
+// column of sw.  Returns nothing: the caller reads sw[slot][tid].
+template <int U>
+__device__ __forceinline__ void fix_group(const FixComp (&re)[kWE], const FixComp (&im)[kWE], int imag, int K,
+                                          long long (*sw)[kWThreads]) {
+  long long W[kWE];
+  if (U == 0) {
+#pragma unroll
+    for (int l = 0; l < kWE; ++l) W[l] = fix_mul(re[l], re[l], K) + fix_mul(im[l], im[l], K);
+    fix_wht<kWE>(W);
+#pragma unroll
+    for (int l = 0; l < kWE; ++l) sw[l][threadIdx.x] = W[l];
+  } else {
+    constexpr int H = fix_high_bit(U), P = kWE / 2;
+    if (!imag) {
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const int l = fix_leader(p, H), m = l ^ U;
+        W[p] = fix_mul(re[l], re[m], K) + fix_mul(im[l], im[m], K);  // Re conj(a_l) a_m
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const int l = fix_leader(p, H), m = l ^ U;
+        W[p] = fix_mul(re[l], im[m], K) - fix_mul(im[l], re[m], K);  // Im conj(a_l) a_m
+      }
+    }
+    fix_wht<P>(W);
+#pragma unroll
+    for (int p = 0; p < P; ++p) sw[p][threadIdx.x] = W[p];
+  }
+}
+
+__device__ __forceinline__ void fix_dispatch(int u, int imag, const FixComp (&re)[kWE], const FixComp (&im)[kWE],
+                                             int K, long long (*sw)[kWThreads]) {
   switch (u) {
-    case 0: fix_products<0>(re, im, W, S, need); break;
-    case 1: fix_products<1>(re, im, W, S, need); break;
-    case 2: fix_products<2>(re, im, W, S, need); break;
-    case 3: fix_products<3>(re, im, W, S, need); break;
-    case 4: fix_products<4>(re, im, W, S, need); break;
-    case 5: fix_products<5>(re, im, W, S, need); break;
-    case 6: fix_products<6>(re, im, W, S, need); break;
-    case 7: fix_products<7>(re, im, W, S, need); break;
+    case 0: fix_group<0>(re, im, imag, K, sw); break;
+    case 1: fix_group<1>(re, im, imag, K, sw); break;
+    case 2: fix_group<2>(re, im, imag, K, sw); break;
+    case 3: fix_group<3>(re, im, imag, K, sw); break;
+    case 4: fix_group<4>(re, im, imag, K, sw); break;
+    case 5: fix_group<5>(re, im, imag, K, sw); break;
+    case 6: fix_group<6>(re, im, imag, K, sw); break;
+    case 7: fix_group<7>(re, im, imag, K, sw); break;
+    case 8: fix_group<8>(re, im, imag, K, sw); break;
+    case 9: fix_group<9>(re, im, imag, K, sw); break;
+    case 10: fix_group<10>(re, im, imag, K, sw); break;
+    case 11: fix_group<11>(re, im, imag, K, sw); break;
+    case 12: fix_group<12>(re, im, imag, K, sw); break;
+    case 13: fix_group<13>(re, im, imag, K, sw); break;
+    case 14: fix_group<14>(re, im, imag, K, sw); break;
+    case 15: fix_group<15>(re, im, imag, K, sw); break;
     default: break;
   }
 }
 
 template <typename Idx>
-__global__ void __launch_bounds__(kFixThreads)
-    k_expval_fix(const float2 *__restrict__ amp, Idx n_cosets, const FixRunDev run,
-                 const FixTermDev *__restrict__ gterms, int S, long long *__restrict__ partials) {
-  constexpr int D = kFixD, E = 1 << D, PAIRS = E / 2, NV = kFixTerms + 1;
-  __shared__ FixTermDev terms[kFixTerms];
-  __shared__ Idx soff[E];
-  // per-term accumulators, one column per thread (conflict-free 8-byte rows)
-  __shared__ long long sacc[NV][kFixThreads];
-  const int nt = run.nterms;
-  if (threadIdx.x < nt) terms[threadIdx.x] = gterms[threadIdx.x];
-  if (threadIdx.x < E) {
+__global__ void __launch_bounds__(kWThreads, 4)
+    k_expval_fix(const float2 *__restrict__ amp, Idx n_tiles, const WhtRunDev run,
+                 const WhtGroupDev *__restrict__ ggroups, const WhtTermDev *__restrict__ gterms, int K,
+                 long long *__restrict__ partials) {
+  __shared__ WhtGroupDev groups[kWGroups];
+  __shared__ Idx tz[kWTerms];
+  __shared__ int tslot[kWTerms];
+  __shared__ Idx soff[kWE];
+  // one column per thread: conflict-free 8-byte rows
+  __shared__ long long sw[kWE][kWThreads];
+  __shared__ long long sacc[kWTerms][kWThreads];
+  const int ng = run.ngroups, nt = run.nterms;
+  if (threadIdx.x < ng) groups[threadIdx.x] = ggroups[threadIdx.x];
+  if (threadIdx.x < nt) {
+    tz[threadIdx.x] = (Idx)gterms[threadIdx.x].z;
+    tslot[threadIdx.x] = gterms[threadIdx.x].slot;
+  }
+  if (threadIdx.x < kWE) {
     uint64_t so = 0;
-    for (int b = 0; b < D; ++b)
+    for (int b = 0; b < kWD; ++b)
       if ((threadIdx.x >> b) & 1) so ^= run.basis[b];
     soff[threadIdx.x] = (Idx)so;
   }
-  for (int j = 0; j < NV; ++j) sacc[j][threadIdx.x] = 0;
+  for (int j = 0; j < kWTerms; ++j) sacc[j][threadIdx.x] = 0;
   __syncthreads();
-  long long nrm = 0;
   const Idx stride = (Idx)gridDim.x * blockDim.x;
-  for (Idx c = (Idx)blockIdx.x * blockDim.x + threadIdx.x; c < n_cosets; c += stride) {
+  for (Idx c = (Idx)blockIdx.x * blockDim.x + threadIdx.x; c < n_tiles; c += stride) {
     Idx rep = c;
 #pragma unroll
-    for (int b = 0; b < D; ++b) {
+    for (int b = 0; b < kWD; ++b) {
       const int pv = run.piv[b];
       rep = ((rep >> pv) << (pv + 1)) | (rep & ((Idx(1) << pv) - 1));
     }
-    FixComp re[E], im[E];
+    FixComp re[kWE], im[kWE];
 #pragma unroll
-    for (int l = 0; l < E; ++l) {
+    for (int l = 0; l < kWE; ++l) {
       const float2 v = amp[rep ^ soff[l]];
       re[l] = fix_split(v.x);
       im[l] = fix_split(v.y);
     }
-    if (run.with_norm) {
+    for (int g = 0; g < ng; ++g) {
+      const WhtGroupDev G = groups[g];
+      // products and shifts depend on the tile only; without this the
+      // compiler hoists every case's products out of the group loop at once
 #pragma unroll
-      for (int l = 0; l < E; ++l) nrm += fix_mul(re[l], re[l], S) + fix_mul(im[l], im[l], S);
-    }
-    long long W[E];
-    int cur = -1;
-    for (int j = 0; j < nt; ++j) {
-      const FixTermDev t = terms[j];
-      if (t.u != cur) {
-        cur = t.u;
-        fix_dispatch(t.u, t.need, re, im, W, S);
+      for (int l = 0; l < kWE; ++l) asm volatile("" : "+r"(re[l].m), "+r"(im[l].m), "+r"(re[l].e), "+r"(im[l].e));
+      fix_dispatch(G.u, G.imag, re, im, K, sw);
+      for (int t = G.t0; t < G.t1; ++t) {
+        const long long v = sw[tslot[t]][threadIdx.x];
+        const long long s = -(long long)(__popcll((unsigned long long)(rep & tz[t])) & 1);
+        sacc[t][threadIdx.x] += (v ^ s) - s;
       }
-      long long sum = 0;
-      if (t.u == 0) {
-#pragma unroll
-        for (int l = 0; l < E; ++l) sum += ((t.psm >> l) & 1u) ? -W[l] : W[l];
-      } else if (t.imag) {
-#pragma unroll
-        for (int q = 0; q < PAIRS; ++q) sum += ((t.psm >> q) & 1u) ? -W[PAIRS + q] : W[PAIRS + q];
-      } else {
-#pragma unroll
-        for (int q = 0; q < PAIRS; ++q) sum += ((t.psm >> q) & 1u) ? -W[q] : W[q];
-      }
-      sacc[j][threadIdx.x] += parity((uint64_t)rep & t.z) ? -sum : sum;
     }
   }
-  sacc[kFixTerms][threadIdx.x] = nrm;
   __syncthreads();
-  // exact block sums: warp w reduces rows w, w + 8, ...
+  // exact block sums: warp w reduces rows w, w + 4, ...
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int j = w; j < NV; j += (int)(blockDim.x >> 5)) {
+  for (int j = w; j < kWTerms; j += (int)(blockDim.x >> 5)) {
     long long v = 0;
     for (int i = lane; i < (int)blockDim.x; i += 32) v += sacc[j][i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) partials[(size_t)blockIdx.x * NV + j] = v;
+    if (lane == 0) partials[(size_t)blockIdx.x * kWTerms + j] = v;
   }
 }
 
 // results[r][j] = sum over blocks of partials[r][b][j]; one CTA per run
 __global__ void k_finish_fix(const long long *__restrict__ partials, int n_blocks, long long *__restrict__ results) {
-  constexpr int NV = kFixTerms + 1;
   __shared__ long long red[kThreads / 32];
-  const long long *p = partials + (size_t)blockIdx.x * n_blocks * NV;
-  for (int j = 0; j < NV; ++j) {
+  const long long *p = partials + (size_t)blockIdx.x * n_blocks * kWTerms;
+  for (int j = 0; j < kWTerms; ++j) {
     long long v = 0;
-    for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) v += p[(size_t)b * NV + j];
+    for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) v += p[(size_t)b * kWTerms + j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -780,62 +828,86 @@ __global__ void k_finish_fix(const long long *__restrict__ partials, int n_block
     if (threadIdx.x == 0) {
       long long t = 0;
       for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-      results[(size_t)blockIdx.x * NV + j] = t;
+      results[(size_t)blockIdx.x * kWTerms + j] = t;
     }
     __syncthreads();
   }
 }
 
-// |a|^2 estimate in FP32 per thread, FP64 per block: only used to pick S
+// |a|^2 estimate in FP32 per thread, FP64 per block: only used to pick S.
+// out[2b] sums the squares as they are; out[2b+1] sums the squares of the
+// components scaled by 2^64 (exact), times 2^-128, which keeps squares down to
+// 2^-254 out of the FP32 underflow range (it overflows once a component
+// reaches 1, and then the unscaled sum is accurate).
 __global__ void __launch_bounds__(kThreads) k_norm_est(const float2 *__restrict__ amp, uint64_t n, double *out) {
-  float acc = 0.f;
+  const float up = 18446744073709551616.0f;  // 2^64
+  float acc = 0.f, accs = 0.f;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const float2 v = amp[i];
     acc = fmaf(v.x, v.x, fmaf(v.y, v.y, acc));
+    const float sx = v.x * up, sy = v.y * up;
+    accs = fmaf(sx, sx, fmaf(sy, sy, accs));
   }
-  double a = acc, b = 0.0;
+  double a = acc, b = (double)accs * 0x1p-128;
   block_sum2(a, b);
-  if (threadIdx.x == 0) out[blockIdx.x] = a;
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = a;
+    out[2 * blockIdx.x + 1] = b;
+  }
 }
 
 struct FixRunHost {
-  FixRunDev dev;
-  std::vector<FixTermDev> terms;
-  std::vector<double> coef;
+  WhtRunDev dev;
+  std::vector<WhtGroupDev> groups;
+  std::vector<WhtTermDev> terms;
+  std::vector<double> coef;  // per term; 0 for the norm
+  int norm_term = -1;        // index of the norm (u = 0, z = 0) in this run, or -1
 };
 
-// group by x (frame signs applied), chunk groups to <= kFixTerms, pack chunks
-// into runs of <= kFixTerms terms whose x-masks span <= kFixD dimensions
+// Group the frame-rewritten terms by (x, part of conj(a_l) a_m they need).
+// The x = 0 terms, led by the norm, fill the first runs; the other groups are
+// packed into runs whose x-masks span <= kWD dimensions (<= kWTerms terms,
+// <= kWGroups groups).  With no x = 0 terms the norm shares the first x-run.
 void plan_fix(const sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c, size_t count,
               std::vector<FixRunHost> &runs) {
   const Pauli &q = sv->frame;
-  std::map<uint64_t, std::vector<Term>> by_x;
+  std::map<std::pair<uint64_t, int>, std::vector<Term>> by;
+  std::vector<Term> diag;
   for (size_t j = 0; j < count; ++j) {
     double cj = c[j];
     if (anticommute(x[j], z[j], q.x, q.z)) cj = -cj;
-    by_x[x[j]].push_back({x[j], z[j], cj});
+    if (x[j] == 0)
+      diag.push_back({0, z[j], cj});
+    else
+      by[{x[j], popc64(x[j] & z[j]) & 1}].push_back({x[j], z[j], cj});
   }
-  std::vector<std::vector<Term>> chunks;
-  for (auto &kv : by_x)
-    for (size_t a = 0; a < kv.second.size(); a += kFixTerms)
-      chunks.emplace_back(kv.second.begin() + a,
-                          kv.second.begin() + std::min(kv.second.size(), a + (size_t)kFixTerms));
+  struct Chunk {
+    uint64_t x;
+    int part;
+    std::vector<Term> t;
+  };
+  std::vector<Chunk> chunks;
+  for (auto &kv : by)
+    for (size_t a = 0; a < kv.second.size(); a += kWTerms)
+      chunks.push_back({kv.first.first, kv.first.second,
+                        std::vector<Term>(kv.second.begin() + a,
+                                          kv.second.begin() + std::min(kv.second.size(), a + (size_t)kWTerms))});
   std::vector<char> used(chunks.size(), 0);
-  size_t left = chunks.size();
-  while (left > 0 || runs.empty()) {
-    FixRunHost r;
-    std::memset(&r.dev, 0, sizeof(r.dev));
-    uint64_t basis[kFixD];
-    int piv[kFixD];
+  size_t left = chunks.size(), di = 0;
+  bool norm_placed = false;
+  while (left > 0 || di < diag.size() || !norm_placed) {
+    uint64_t basis[kWD];
+    int piv[kWD];
     int d = 0;
     auto reduce = [&](uint64_t v) {
       for (int b = 0; b < d; ++b)
         if ((v >> piv[b]) & 1ULL) v ^= basis[b];
       return v;
     };
-    auto add_vec = [&](uint64_t rr, uint64_t) {
-      int pv = 63 - __builtin_clzll(rr);
+    // reduced echelon form: pivot = highest bit, absent from every other vector
+    auto add_vec = [&](uint64_t rr) {
+      const int pv = 63 - __builtin_clzll(rr);
       for (int b = 0; b < d; ++b)
         if ((basis[b] >> pv) & 1ULL) basis[b] ^= rr;
       int pos = d;
@@ -848,145 +920,174 @@ void plan_fix(const sv_state *sv, const uint64_t *x, const uint64_t *z, const do
       piv[pos] = pv;
       ++d;
     };
+    const bool has_norm = !norm_placed;
+    norm_placed = true;
+    size_t nterm = has_norm ? 1 : 0;
+    std::vector<Term> zt;
+    while (di < diag.size() && nterm < (size_t)kWTerms) {
+      zt.push_back(diag[di++]);
+      ++nterm;
+    }
+    // x = 0 terms first, in runs of their own: every run holding one pays for
+    // the 16-entry |a|^2 transform, so they are not spread over the x-runs
     std::vector<size_t> members;
-    size_t nterm = 0;
-    for (size_t g = 0; g < chunks.size(); ++g) {
-      if (used[g]) continue;
-      if (nterm + chunks[g].size() > (size_t)kFixTerms) continue;
-      uint64_t rr = reduce(chunks[g][0].x);
+    for (size_t g = 0; g < chunks.size() && zt.empty() && members.size() + 1 < (size_t)kWGroups; ++g) {
+      if (used[g] || nterm + chunks[g].t.size() > (size_t)kWTerms) continue;
+      const uint64_t rr = reduce(chunks[g].x);
       if (rr != 0) {
-        if (d >= kFixD) continue;
-        add_vec(rr, 0);
+        if (d >= kWD) continue;
+        add_vec(rr);
       }
       used[g] = 1;
       --left;
       members.push_back(g);
-      nterm += chunks[g].size();
-      if (nterm == (size_t)kFixTerms) break;
+      nterm += chunks[g].t.size();
+      if (nterm == (size_t)kWTerms) break;
     }
-    // pad to kFixD with the highest unused bits
+    // pad to kWD with the highest unused index bits (keeps low bits for coalescing)
     uint64_t usedbits = 0;
     for (int b = 0; b < d; ++b) usedbits |= 1ULL << piv[b];
-    for (int bit = sv->n - 1; bit >= 0 && d < kFixD; --bit)
+    for (int bit = sv->n - 1; bit >= 0 && d < kWD; --bit)
       if (!((usedbits >> bit) & 1ULL)) {
-        add_vec(1ULL << bit, 0);
+        add_vec(1ULL << bit);
         usedbits |= 1ULL << bit;
       }
-    r.dev.d = d;
-    for (int b = 0; b < d; ++b) {
+    FixRunHost r;
+    std::memset(&r.dev, 0, sizeof(r.dev));
+    for (int b = 0; b < kWD; ++b) {
       r.dev.basis[b] = basis[b];
       r.dev.piv[b] = piv[b];
     }
-    // terms sorted by u so a run recomputes products only when u changes
-    std::vector<std::pair<int, const Term *>> ts;
-    for (size_t g : members)
-      for (const Term &t : chunks[g]) {
-        int u = 0;
-        for (int b = 0; b < d; ++b)
-          if ((t.x >> piv[b]) & 1ULL) u |= 1 << b;
-        ts.push_back({u, &t});
-      }
-    std::stable_sort(ts.begin(), ts.end(), [](const auto &a1, const auto &b1) { return a1.first < b1.first; });
-    std::map<int, int> need;
-    for (auto &ut : ts) {
-      const int ny = popc64(ut.second->x & ut.second->z) & 3;
-      need[ut.first] |= ut.first == 0 ? 1 : ((ny & 1) ? 2 : 1);
-    }
-    for (auto &ut : ts) {
-      const Term &t = *ut.second;
-      const int u = ut.first;
-      FixTermDev e;
-      e.z = t.z;
-      e.u = u;
-      e.need = need[u];
-      uint32_t psm = 0;
-      auto sgn = [&](int l) {
-        uint64_t so = 0;
-        for (int b = 0; b < d; ++b)
-          if ((l >> b) & 1) so ^= basis[b];
-        return (uint32_t)(popc64(so & t.z) & 1);
-      };
-      const int ny = popc64(t.x & t.z) & 3;
-      if (u == 0) {
-        for (int l = 0; l < (1 << kFixD); ++l) psm |= sgn(l) << l;
-        e.imag = 0;
-        r.coef.push_back(t.c);
-      } else {
-        int H = 0;
-        while (u >> (H + 1)) ++H;
-        for (int p = 0; p < (1 << kFixD) / 2; ++p) psm |= sgn(fix_leader(p, H)) << p;
-        e.imag = ny & 1;
-        r.coef.push_back(2.0 * t.c * ((ny == 0 || ny == 1) ? 1.0 : -1.0));
-      }
-      e.psm = psm;
+    auto zeta = [&](uint64_t zz) {
+      int v = 0;
+      for (int b = 0; b < kWD; ++b) v |= (int)(popc64(basis[b] & zz) & 1) << b;
+      return v;
+    };
+    auto open_group = [&](int u, int imag) {
+      WhtGroupDev g;
+      g.u = u;
+      g.imag = imag;
+      g.t0 = g.t1 = (int32_t)r.terms.size();
+      r.groups.push_back(g);
+    };
+    auto add_term = [&](uint64_t zz, int slot, double cf) {
+      WhtTermDev e;
+      e.z = zz;
+      e.slot = slot;
+      e.pad = 0;
       r.terms.push_back(e);
+      r.coef.push_back(cf);
+      r.groups.back().t1 = (int32_t)r.terms.size();
+    };
+    if (has_norm || !zt.empty()) {
+      open_group(0, 0);
+      if (has_norm) {
+        r.norm_term = (int)r.terms.size();
+        add_term(0, 0, 0.0);
+      }
+      for (const Term &t : zt) add_term(t.z, zeta(t.z), t.c);
     }
+    // groups in ascending (u, part) order
+    std::vector<std::pair<int, size_t>> order;
+    for (size_t g : members) {
+      int u = 0;
+      for (int b = 0; b < kWD; ++b)
+        if ((chunks[g].x >> piv[b]) & 1ULL) u |= 1 << b;
+      order.push_back({u * 2 + chunks[g].part, g});
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<int, size_t> &a1, const std::pair<int, size_t> &b1) { return a1.first < b1.first; });
+    for (auto &ug : order) {
+      const int u = ug.first >> 1;
+      const Chunk &ch = chunks[ug.second];
+      const int H = fix_high_bit(u);
+      open_group(u, ch.part);
+      for (const Term &t : ch.t) {
+        const int zb = zeta(t.z);
+        const int slot = (zb & ((1 << H) - 1)) | ((zb >> (H + 1)) << H);
+        const int ny = popc64(t.x & t.z) & 3;
+        add_term(t.z, slot, 2.0 * t.c * ((ny == 0 || ny == 1) ? 1.0 : -1.0));
+      }
+    }
+    r.dev.ngroups = (int32_t)r.groups.size();
     r.dev.nterms = (int32_t)r.terms.size();
-    r.dev.with_norm = runs.empty() ? 1 : 0;
     runs.push_back(std::move(r));
-    if (left == 0) break;
   }
 }
 
 template <typename Idx>
 int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *energy, double *norm2) {
-  constexpr int NV = kFixTerms + 1;
   static int cap = 0;
   if (!cap) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expval_fix<Idx>, kFixThreads, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expval_fix<Idx>, kWThreads, 0) != cudaSuccess) {
       cudaGetLastError();
       per_sm = 1;
     }
     cap = (per_sm > 0 ? per_sm : 1) * device_sm_count();
   }
   const uint64_t n_amps = 1ULL << sv->n;
-  const uint64_t n_cosets = n_amps >> kFixD;
-  uint64_t need = (n_cosets + kFixThreads - 1) / kFixThreads;
+  const uint64_t n_tiles = n_amps >> kWD;
+  const uint64_t need = (n_tiles + kWThreads - 1) / kWThreads;
   const int blocks = (int)(need < (uint64_t)cap ? (need ? need : 1) : cap);
-  const int est_blocks = 64;
+  const int est_blocks = 512;
   // partial sums (int64) and the S estimate share the double scratch
-  int rc = ensure_scratch(sv, (size_t)NV * blocks * runs.size() + est_blocks, NV * runs.size() + est_blocks);
+  int rc = ensure_scratch(sv, (size_t)kWTerms * blocks * runs.size(), kWTerms * runs.size() + 2 * est_blocks);
   if (rc) return rc;
-  // stage terms
+  // stage groups (a fixed kWGroups block) and terms of every run
+  constexpr size_t kGroupBytes = sizeof(WhtGroupDev) * kWGroups;
   size_t bytes = 0;
   std::vector<size_t> off(runs.size());
   for (size_t r = 0; r < runs.size(); ++r) {
     off[r] = bytes;
-    bytes += ((runs[r].terms.size() * sizeof(FixTermDev)) + 15) & ~size_t(15);
+    bytes += kGroupBytes + runs[r].terms.size() * sizeof(WhtTermDev);
   }
-  if (!bytes) bytes = 16;
   PR_CUDA(cudaStreamSynchronize(sv->stream));
   rc = ensure_stage(sv, bytes);
   if (rc) return rc;
-  for (size_t r = 0; r < runs.size(); ++r)
+  for (size_t r = 0; r < runs.size(); ++r) {
+    char *dst = (char *)sv->h_stage + off[r];
+    std::memset(dst, 0, kGroupBytes);
+    std::memcpy(dst, runs[r].groups.data(), runs[r].groups.size() * sizeof(WhtGroupDev));
     if (!runs[r].terms.empty())
-      std::memcpy((char *)sv->h_stage + off[r], runs[r].terms.data(), runs[r].terms.size() * sizeof(FixTermDev));
+      std::memcpy(dst + kGroupBytes, runs[r].terms.data(), runs[r].terms.size() * sizeof(WhtTermDev));
+  }
   PR_CUDA(cudaMemcpyAsync(sv->d_stage, sv->h_stage, bytes, cudaMemcpyHostToDevice, sv->stream));
   // choose S from an estimate of <a|a>
-  double *est = sv->d_results + NV * runs.size();
+  double *d_est = sv->d_results + kWTerms * runs.size();
   {
     const int tr = trace_begin(sv);
-    k_norm_est<<<est_blocks, kThreads, 0, sv->stream>>>((const float2 *)sv->amps, n_amps, est);
+    k_norm_est<<<est_blocks, kThreads, 0, sv->stream>>>((const float2 *)sv->amps, n_amps, d_est);
     PR_CHECK_LAUNCH();
     trace_end(sv, tr, KN_EXPVAL, 8.0 * (double)n_amps);
   }
-  PR_CUDA(cudaMemcpyAsync(sv->h_results, est, est_blocks * sizeof(double), cudaMemcpyDeviceToHost, sv->stream));
+  PR_CUDA(cudaMemcpyAsync(sv->h_results, d_est, 2 * est_blocks * sizeof(double), cudaMemcpyDeviceToHost, sv->stream));
   PR_CUDA(cudaStreamSynchronize(sv->stream));
-  double nest = 0.0;
-  for (int i = 0; i < est_blocks; ++i) nest += sv->h_results[i];
-  // S = 60 - ceil(log2 <a|a>) (estimate widened by 1 %): every per-term sum is
-  // bounded by <a|a> 2^S <= 2^60 and no product needs a left shift
-  int S = 60;
-  if (nest * 1.01 > 1.0) S = 60 - (int)std::ceil(std::log2(nest * 1.01));
+  double plain = 0.0, scaled = 0.0;
+  for (int i = 0; i < est_blocks; ++i) {
+    plain += sv->h_results[2 * i];
+    scaled += sv->h_results[2 * i + 1];
+  }
+  if (!std::isfinite(plain)) return fail(SV_EUNSUPPORTED, "state norm is not finite in FP32");
+  const double nest = std::isfinite(scaled) ? scaled : plain;
+  // S = 60 - ceil(log2 <a|a>) (estimate widened by 2 %): every per-term sum,
+  // and every intermediate of the tile transforms, is bounded by
+  // <a|a> 2^S <= 2^60, and no product needs a left shift.  Each thread of
+  // k_norm_est sums at most 2^(n-17) FP32 squares (relative error < 0.2 % for
+  // n <= 32).  The scaled sum loses squares below 2^-254, at most 2^(n-254) of
+  // mass, under 0.8 % of any estimate above 2^(n-247), which therefore bounds
+  // S; the unscaled sum is used only when it is at least about 1.
+  const double est = std::max(nest, std::ldexp(1.0, sv->n - 247));
+  const int S = 60 - (int)std::ceil(std::log2(est * 1.02));
   if (S < 8) return fail(SV_EUNSUPPORTED, "state norm %g too large for the fixed-point sums", nest);
   long long *part = (long long *)sv->d_partials;
   long long *res = (long long *)sv->d_results;
   for (size_t r = 0; r < runs.size(); ++r) {
+    const char *base = (const char *)sv->d_stage + off[r];
     const int tr = trace_begin(sv);
-    k_expval_fix<Idx><<<blocks, kFixThreads, 0, sv->stream>>>(
-        (const float2 *)sv->amps, (Idx)n_cosets, runs[r].dev, (const FixTermDev *)((char *)sv->d_stage + off[r]), S,
-        part + (size_t)NV * blocks * r);
+    k_expval_fix<Idx><<<blocks, kWThreads, 0, sv->stream>>>(
+        (const float2 *)sv->amps, (Idx)n_tiles, runs[r].dev, (const WhtGroupDev *)base,
+        (const WhtTermDev *)(base + kGroupBytes), 14 - S, part + (size_t)kWTerms * blocks * r);
     PR_CHECK_LAUNCH();
     trace_end(sv, tr, KN_EXPVAL, 8.0 * (double)n_amps);
   }
@@ -994,18 +1095,20 @@ int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *ener
     const int tr = trace_begin(sv);
     k_finish_fix<<<(unsigned)runs.size(), kThreads, 0, sv->stream>>>(part, blocks, res);
     PR_CHECK_LAUNCH();
-    trace_end(sv, tr, KN_FINISH, 8.0 * NV * blocks * runs.size());
+    trace_end(sv, tr, KN_FINISH, 8.0 * kWTerms * blocks * runs.size());
   }
-  PR_CUDA(cudaMemcpyAsync(sv->h_results, res, NV * runs.size() * sizeof(long long), cudaMemcpyDeviceToHost,
+  PR_CUDA(cudaMemcpyAsync(sv->h_results, res, kWTerms * runs.size() * sizeof(long long), cudaMemcpyDeviceToHost,
                           sv->stream));
   PR_CUDA(cudaStreamSynchronize(sv->stream));
   const long long *h = (const long long *)sv->h_results;
   const double unit = std::ldexp(1.0, -S);
-  long double e = 0.0L;
-  for (size_t r = 0; r < runs.size(); ++r)
-    for (size_t j = 0; j < runs[r].coef.size(); ++j) e += (long double)runs[r].coef[j] * (long double)h[r * NV + j];
+  long double e = 0.0L, nrm = 0.0L;
+  for (size_t r = 0; r < runs.size(); ++r) {
+    for (size_t j = 0; j < runs[r].coef.size(); ++j) e += (long double)runs[r].coef[j] * (long double)h[r * kWTerms + j];
+    if (runs[r].norm_term >= 0) nrm += (long double)h[r * kWTerms + runs[r].norm_term];
+  }
   if (energy) *energy = (double)(e * unit);
-  if (norm2) *norm2 = (double)h[kFixTerms] * unit;
+  if (norm2) *norm2 = (double)(nrm * unit);
   return SV_OK;
 }
 
@@ -1013,7 +1116,7 @@ int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *ener
 
 int expval_impl(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c, size_t count,
                 double *energy, double *norm2) {
-  if (sv->dtype == SV_C64 && sv->n >= kFixD) {
+  if (sv->dtype == SV_C64 && sv->n >= kWD) {
     if (count && (!x || !z || !c)) return fail(SV_EINVAL, "NULL term arrays");
     int rc = validate_masks(sv->n, x, z, count);
     if (rc) return rc;
