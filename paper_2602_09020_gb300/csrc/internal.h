@@ -78,8 +78,12 @@ struct RotDev {
   uint64_t x, z;
   double t;
   uint32_t zt;
-  uint32_t code;
+  uint32_t code;  // (u << 1) | imag, plus kPairFirst
 };
+// code flag: this rotation and the next one in the run have the same code
+// (same pairing and part), so a kernel may apply both in one sweep of the pairs
+constexpr uint32_t kPairFirst = 1u << 16;
+constexpr uint32_t kCodeMask = kPairFirst - 1;
 static_assert(sizeof(RotDev) == 32, "RotDev layout");
 
 // One rotation of a diagonal phase-sum run: a = theta/2 as a fixed-point

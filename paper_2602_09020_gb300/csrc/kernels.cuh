@@ -116,7 +116,7 @@ __device__ __forceinline__ void body_coset(typename Cx<R>::T *__restrict__ amp, 
     RotSm<R, Idx> s;
     s.z = (Idx)r.z;
     s.zt = r.zt;
-    s.code = r.code;
+    s.code = r.code & kCodeMask;
     s.t = (R)t;
     srot[j] = s;
   }
@@ -297,6 +297,81 @@ __device__ __forceinline__ void dispatch_x2(uint32_t code, float2 (&RE)[1 << D],
   }
 }
 
+// Two consecutive rotations with the same code, T for the first and V for the
+// second, applied pair by pair (pairs are disjoint, so the order of the two
+// sweeps does not matter).  The first writes each leader's new value to a
+// temporary and the second writes it back to the leader's register: unlike
+// one rotation at a time, the update needs no register copies.
+template <int D, int U, int IMAG>
+__device__ __forceinline__ void apply_x2_pair(float2 (&RE)[1 << D], float2 (&IM)[1 << D], float2 T,
+                                              const float2 (&S)[D > 0 ? D : 1], float2 V,
+                                              const float2 (&SV)[D > 0 ? D : 1]) {
+  if constexpr (U == 0) {
+#pragma unroll
+    for (int i = 0; i < (1 << D); ++i) {
+      if (i > 0) {
+        T = __fmul2_rn(T, S[ctz_c(i)]);
+        V = __fmul2_rn(V, SV[ctz_c(i)]);
+      }
+      const int l = i ^ (i >> 1);
+      const float2 re = RE[l], im = IM[l];
+      const float2 re1 = __ffma2_rn(neg2(T), im, re), im1 = __ffma2_rn(T, re, im);
+      RE[l] = __ffma2_rn(neg2(V), im1, re1);
+      IM[l] = __ffma2_rn(V, re1, im1);
+    }
+  } else {
+    constexpr int H = high_bit(U);
+#pragma unroll
+    for (int i = 0; i < (1 << (D - 1)); ++i) {
+      if (i > 0) {
+        T = __fmul2_rn(T, S[free_bit<H>(ctz_c(i))]);
+        V = __fmul2_rn(V, SV[free_bit<H>(ctz_c(i))]);
+      }
+      const float2 N = neg2(T), NV = neg2(V);
+      const int l = gray_leader<D, H>(i);
+      const int m = l ^ U;
+      const float2 rl = RE[l], il = IM[l], rm = RE[m], im = IM[m];
+      if (IMAG) {
+        const float2 rl1 = __ffma2_rn(N, im, rl), il1 = __ffma2_rn(T, rm, il);
+        const float2 rm1 = __ffma2_rn(N, il, rm), im1 = __ffma2_rn(T, rl, im);
+        RE[l] = __ffma2_rn(NV, im1, rl1);
+        IM[l] = __ffma2_rn(V, rm1, il1);
+        RE[m] = __ffma2_rn(NV, il1, rm1);
+        IM[m] = __ffma2_rn(V, rl1, im1);
+      } else {
+        const float2 rl1 = __ffma2_rn(T, rm, rl), il1 = __ffma2_rn(T, im, il);
+        const float2 rm1 = __ffma2_rn(N, rl, rm), im1 = __ffma2_rn(N, il, im);
+        RE[l] = __ffma2_rn(V, rm1, rl1);
+        IM[l] = __ffma2_rn(V, im1, il1);
+        RE[m] = __ffma2_rn(NV, rl1, rm1);
+        IM[m] = __ffma2_rn(NV, il1, im1);
+      }
+    }
+  }
+}
+
+#define PR_CASE2P(K)                                                               \
+  case K:                                                                          \
+    if constexpr ((((K) >> 1) < (1 << D)) && ((((K) >> 1) != 0) || ((K)&1)))       \
+      apply_x2_pair<D, ((K) >> 1), ((K)&1)>(RE, IM, T, S, V, SV);                 \
+    break;
+#define PR_CASE2P_8(B) \
+  PR_CASE2P(B + 0) PR_CASE2P(B + 1) PR_CASE2P(B + 2) PR_CASE2P(B + 3) PR_CASE2P(B + 4) PR_CASE2P(B + 5) PR_CASE2P(B + 6) PR_CASE2P(B + 7)
+
+template <int D>
+__device__ __forceinline__ void dispatch_x2_pair(uint32_t code, float2 (&RE)[1 << D], float2 (&IM)[1 << D],
+                                                 float2 T, const float2 (&S)[D > 0 ? D : 1], float2 V,
+                                                 const float2 (&SV)[D > 0 ? D : 1]) {
+  switch (code) {
+    PR_CASE2P_8(0)
+    PR_CASE2P_8(8)
+    PR_CASE2P_8(16)
+    PR_CASE2P_8(24)
+    default:
+      break;
+  }
+}
+
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -406,7 +481,20 @@ __device__ __forceinline__ void body_c64x2(float4 *__restrict__ amp4, Idx n_pair
       float2 S[D > 0 ? D : 1];
 #pragma unroll
       for (int b = 0; b < (D > 0 ? D : 1); ++b) S[b] = s.S[b];
-      dispatch_x2<D>(s.code, RE, IM, T, S);
+      const uint32_t code = s.code;
+      if (code & kPairFirst) {
+        const RotSm2<Idx> &s2 = srot[j + 1];
+        const Idx z2 = s2.z;
+        const int p2 = parity(rep & z2);
+        const float2 V = s2.tt[p2 | ((p2 ^ (int)(z2 & 1)) << 1)];
+        float2 SV[D > 0 ? D : 1];
+#pragma unroll
+        for (int b = 0; b < (D > 0 ? D : 1); ++b) SV[b] = s2.S[b];
+        dispatch_x2_pair<D>(code & kCodeMask, RE, IM, T, S, V, SV);
+        ++j;
+      } else {
+        dispatch_x2<D>(code, RE, IM, T, S);
+      }
     }
     if (run.fold) {
       const float fr = (float)run.fold_re, fi = (float)run.fold_im;

@@ -190,6 +190,15 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
       d.code = (u << 1) | (uint32_t)imag;
       rots.push_back(d);
     }
+    // greedy pairs of consecutive rotations with the same code
+    for (size_t i = (size_t)r.first; i + 1 < rots.size();) {
+      if (rots[i].code == rots[i + 1].code) {
+        rots[i].code |= kPairFirst;
+        i += 2;
+      } else {
+        ++i;
+      }
+    }
     growth_since_fold += rb.growth;
     if (force_fold || growth_since_fold > gcap) {
       r.fold = 1;
