@@ -78,12 +78,14 @@ struct RotDev {
   uint64_t x, z;
   double t;
   uint32_t zt;
-  uint32_t code;  // (u << 1) | imag, plus kPairFirst
+  uint32_t code;  // (u << 1) | imag in the low 16 bits; segment length above
 };
-// code flag: this rotation and the next one in the run have the same code
-// (same pairing and part), so a kernel may apply both in one sweep of the pairs
-constexpr uint32_t kPairFirst = 1u << 16;
-constexpr uint32_t kCodeMask = kPairFirst - 1;
+// A segment is a stretch of consecutive rotations of a run with the same code
+// (same pairing and part).  Its first rotation carries the stretch length in
+// the bits above kCodeMask (the others carry 0 there), so a kernel can apply
+// the whole segment under one dispatch, two rotations per sweep of the pairs.
+constexpr int kSegShift = 16;
+constexpr uint32_t kCodeMask = (1u << kSegShift) - 1;
 static_assert(sizeof(RotDev) == 32, "RotDev layout");
 
 // One rotation of a diagonal phase-sum run: a = theta/2 as a fixed-point

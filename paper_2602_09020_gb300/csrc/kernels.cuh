@@ -196,15 +196,23 @@ __device__ __forceinline__ void body_coset(typename Cx<R>::T *__restrict__ amp, 
 // so walking the pair leaders in Gray-code order updates the coefficient with one
 // packed multiply by +-1 per pair instead of a per-element select.
 
-// per-rotation values shared by the CTA: tt[p0 | p1 << 1] = (+-t, +-t) for the
-// two coset parities, S[b] = (s_b, s_b) with s_b = (-1)^{popc(basis_b & z)}
+// per-rotation values shared by the CTA: t2 = (t, t (-1)^{z_0}) (a thread's
+// two cosets differ in index bit 0), S[b] = (s_b, s_b) with
+// s_b = (-1)^{popc(basis_b & z)}; three 16-byte loads for 32-bit indices
 template <typename Idx>
-struct RotSm2 {
+struct alignas(16) RotSm2 {
+  float2 t2;
   Idx z;
   uint32_t code;
-  float2 tt[4];
   float2 S[4];
 };
+
+// the thread's coefficient: t2 with both signs flipped when popc(rep & z) is odd
+template <typename Idx>
+__device__ __forceinline__ float2 rot_t(const RotSm2<Idx> &s, Idx rep) {
+  const uint32_t sg = (uint32_t)parity(rep & s.z) << 31;
+  return make_float2(__uint_as_float(__float_as_uint(s.t2.x) ^ sg), __uint_as_float(__float_as_uint(s.t2.y) ^ sg));
+}
 
 // free-bit index k (0-based among bits != H) -> bit position
 template <int H>
@@ -276,27 +284,6 @@ __device__ __forceinline__ void apply_x2(float2 (&RE)[1 << D], float2 (&IM)[1 <<
   }
 }
 
-#define PR_CASE2(K)                                                                \
-  case K:                                                                          \
-    if constexpr ((((K) >> 1) < (1 << D)) && ((((K) >> 1) != 0) || ((K)&1)))       \
-      apply_x2<D, ((K) >> 1), ((K)&1)>(RE, IM, T, S);                           \
-    break;
-#define PR_CASE2_8(B) \
-  PR_CASE2(B + 0) PR_CASE2(B + 1) PR_CASE2(B + 2) PR_CASE2(B + 3) PR_CASE2(B + 4) PR_CASE2(B + 5) PR_CASE2(B + 6) PR_CASE2(B + 7)
-
-template <int D>
-__device__ __forceinline__ void dispatch_x2(uint32_t code, float2 (&RE)[1 << D], float2 (&IM)[1 << D], float2 T,
-                                            const float2 (&S)[D > 0 ? D : 1]) {
-  switch (code) {
-    PR_CASE2_8(0)
-    PR_CASE2_8(8)
-    PR_CASE2_8(16)
-    PR_CASE2_8(24)
-    default:
-      break;
-  }
-}
-
 // Two consecutive rotations with the same code, T for the first and V for the
 // second, applied pair by pair (pairs are disjoint, so the order of the two
 // sweeps does not matter).  The first writes each leader's new value to a
@@ -350,23 +337,48 @@ __device__ __forceinline__ void apply_x2_pair(float2 (&RE)[1 << D], float2 (&IM)
   }
 }
 
-#define PR_CASE2P(K)                                                               \
+// One segment (len consecutive rotations with code (U << 1) | IMAG): two
+// rotations per sweep of the pairs, the odd one out alone.
+template <typename Idx, int D, int U, int IMAG>
+__device__ __forceinline__ void seg_x2(float2 (&RE)[1 << D], float2 (&IM)[1 << D], const RotSm2<Idx> *r, int len,
+                                       Idx rep) {
+  constexpr int NS = D > 0 ? D : 1;
+  int k = 0;
+  for (; k + 1 < len; k += 2) {
+    const RotSm2<Idx> &a = r[k], &b = r[k + 1];
+    float2 S[NS], SV[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      S[q] = a.S[q];
+      SV[q] = b.S[q];
+    }
+    apply_x2_pair<D, U, IMAG>(RE, IM, rot_t(a, rep), S, rot_t(b, rep), SV);
+  }
+  if (k < len) {
+    const RotSm2<Idx> &a = r[k];
+    float2 S[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) S[q] = a.S[q];
+    apply_x2<D, U, IMAG>(RE, IM, rot_t(a, rep), S);
+  }
+}
+
+#define PR_CASE2S(K)                                                               \
   case K:                                                                          \
     if constexpr ((((K) >> 1) < (1 << D)) && ((((K) >> 1) != 0) || ((K)&1)))       \
-      apply_x2_pair<D, ((K) >> 1), ((K)&1)>(RE, IM, T, S, V, SV);                 \
+      seg_x2<Idx, D, ((K) >> 1), ((K)&1)>(RE, IM, r, len, rep);                   \
     break;
-#define PR_CASE2P_8(B) \
-  PR_CASE2P(B + 0) PR_CASE2P(B + 1) PR_CASE2P(B + 2) PR_CASE2P(B + 3) PR_CASE2P(B + 4) PR_CASE2P(B + 5) PR_CASE2P(B + 6) PR_CASE2P(B + 7)
+#define PR_CASE2S_8(B) \
+  PR_CASE2S(B + 0) PR_CASE2S(B + 1) PR_CASE2S(B + 2) PR_CASE2S(B + 3) PR_CASE2S(B + 4) PR_CASE2S(B + 5) PR_CASE2S(B + 6) PR_CASE2S(B + 7)
 
-template <int D>
-__device__ __forceinline__ void dispatch_x2_pair(uint32_t code, float2 (&RE)[1 << D], float2 (&IM)[1 << D],
-                                                 float2 T, const float2 (&S)[D > 0 ? D : 1], float2 V,
-                                                 const float2 (&SV)[D > 0 ? D : 1]) {
+template <typename Idx, int D>
+__device__ __forceinline__ void dispatch_seg(uint32_t code, float2 (&RE)[1 << D], float2 (&IM)[1 << D],
+                                             const RotSm2<Idx> *r, int len, Idx rep) {
   switch (code) {
-    PR_CASE2P_8(0)
-    PR_CASE2P_8(8)
-    PR_CASE2P_8(16)
-    PR_CASE2P_8(24)
+    PR_CASE2S_8(0)
+    PR_CASE2S_8(8)
+    PR_CASE2S_8(16)
+    PR_CASE2S_8(24)
     default:
       break;
   }
@@ -417,12 +429,9 @@ __device__ __forceinline__ void body_c64x2(float4 *__restrict__ amp4, Idx n_pair
     if (__popcll((r.x & fz) ^ (r.z & fx)) & 1) t = -t;  // runtime frame sign
     const float tf = (float)t;
     RotSm2<Idx> s;
+    s.t2 = make_float2(tf, (r.z & 1) ? -tf : tf);
     s.z = (Idx)r.z;
     s.code = r.code;
-    s.tt[0] = make_float2(tf, tf);
-    s.tt[1] = make_float2(-tf, tf);
-    s.tt[2] = make_float2(tf, -tf);
-    s.tt[3] = make_float2(-tf, -tf);
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const float sb = (b < D && ((r.zt >> (1 << b)) & 1u)) ? -1.0f : 1.0f;
@@ -472,29 +481,11 @@ __device__ __forceinline__ void body_c64x2(float4 *__restrict__ amp4, Idx n_pair
       for (int l = 0; l < E; ++l) cp_async16(slot + l * blockDim.x, amp4 + ((repn ^ soff[l]) >> 1));
       cp_async_commit();
     }
-    for (int j = 0; j < count; ++j) {
-      const RotSm2<Idx> &s = srot[j];
-      const Idx z = s.z;
-      const int p0 = parity(rep & z);
-      const int q = p0 | ((p0 ^ (int)(z & 1)) << 1);
-      const float2 T = s.tt[q];
-      float2 S[D > 0 ? D : 1];
-#pragma unroll
-      for (int b = 0; b < (D > 0 ? D : 1); ++b) S[b] = s.S[b];
-      const uint32_t code = s.code;
-      if (code & kPairFirst) {
-        const RotSm2<Idx> &s2 = srot[j + 1];
-        const Idx z2 = s2.z;
-        const int p2 = parity(rep & z2);
-        const float2 V = s2.tt[p2 | ((p2 ^ (int)(z2 & 1)) << 1)];
-        float2 SV[D > 0 ? D : 1];
-#pragma unroll
-        for (int b = 0; b < (D > 0 ? D : 1); ++b) SV[b] = s2.S[b];
-        dispatch_x2_pair<D>(code & kCodeMask, RE, IM, T, S, V, SV);
-        ++j;
-      } else {
-        dispatch_x2<D>(code, RE, IM, T, S);
-      }
+    for (int j = 0; j < count;) {
+      const uint32_t word = srot[j].code;
+      const int len = (int)(word >> kSegShift);
+      dispatch_seg<Idx, D>(word & kCodeMask, RE, IM, srot + j, len, rep);
+      j += len > 0 ? len : 1;
     }
     if (run.fold) {
       const float fr = (float)run.fold_re, fi = (float)run.fold_im;

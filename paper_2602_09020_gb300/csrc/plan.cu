@@ -190,14 +190,12 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
       d.code = (u << 1) | (uint32_t)imag;
       rots.push_back(d);
     }
-    // greedy pairs of consecutive rotations with the same code
-    for (size_t i = (size_t)r.first; i + 1 < rots.size();) {
-      if (rots[i].code == rots[i + 1].code) {
-        rots[i].code |= kPairFirst;
-        i += 2;
-      } else {
-        ++i;
-      }
+    // segments: stretches of consecutive rotations with the same code
+    for (size_t i = (size_t)r.first; i < rots.size();) {
+      size_t e = i + 1;
+      while (e < rots.size() && rots[e].code == rots[i].code) ++e;
+      rots[i].code |= (uint32_t)(e - i) << kSegShift;
+      i = e;
     }
     growth_since_fold += rb.growth;
     if (force_fold || growth_since_fold > gcap) {
