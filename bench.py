@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import hashlib
 import json
 import os
 import statistics
@@ -84,12 +85,35 @@ def peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def ncu_traffic() -> dict:
+# source files that define each traced kernel family: a stored ncu traffic
+# figure counts only while these are unchanged since the capture
+KERNEL_SOURCES = {"k_coset": ("kernels.cuh", "rotate.cu"), "k_diag_sum": ("kernels.cuh", "rotate.cu"),
+                  "k_expval": ("reduce.cu",)}
+
+
+def kernel_source_digest(name: str):
+    for prefix, files in KERNEL_SOURCES.items():
+        if name.startswith(prefix):
+            h = hashlib.sha256()
+            for f in files:
+                with open(os.path.join(ROOT, "paper_2602_09020_gb300", "csrc", f), "rb") as fh:
+                    h.update(fh.read())
+            return h.hexdigest()
+    return None
+
+
+def ncu_traffic(name: str, dtype: str, n: int):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one
+    ncu capture of this kernel at this size, or None when there is none or the
+    kernel's sources changed after it was taken."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if os.path.exists(p):
-        with open(p) as fh:
-            return json.load(fh)
-    return {}
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        entry = json.load(fh).get(f"{name}/{dtype}/n{n}")
+    if not entry or entry.get("sources_sha256") != kernel_source_digest(name):
+        return None
+    return entry["dram_bytes_per_launch"]
 
 
 # ------------------------------------------------------------------ clocks
@@ -272,7 +296,7 @@ def run_ours(a):
             return None, 0
         name = max(rows, key=lambda k: rows[k][1])
         launches, tot_ms, by, fl = rows[name]
-        traffic = ncu_traffic().get(f"{name}/{dtype}/n{a.n}")
+        traffic = ncu_traffic(name, dtype, a.n)
         common = {"kernel": name, "traffic": traffic, "launches_per_step": launches / steps,
                   "ms_per_launch": tot_ms / launches, "algorithmic_bytes_per_launch": by / launches,
                   "algorithmic_flops_per_launch": fl / launches,
@@ -401,7 +425,10 @@ def run_ours(a):
 
 def batch_measure(capi, torch, stream, sh, barrier, reps: int = 3):
     """64 independent JW-shaped problems, n ~ U{12..22}, complex64, T ~ U{100..800},
-    dt ~ U[0.01, 0.2], 1..8 first-order steps each."""
+    dt ~ U[0.01, 0.2], 1..8 first-order steps each.  The states live on a stream
+    of their own: the legacy default stream cannot be captured into a graph."""
+    own = torch.cuda.Stream()
+    sh = int(own.cuda_stream)
     wl = synth.batch_workload(64, seed=4)
     states, plans, total = [], [], 0
     for circ in wl:
