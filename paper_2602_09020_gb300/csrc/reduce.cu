@@ -594,7 +594,8 @@ int prepare(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c,
 // coefficients c_j multiply the exact per-term sums on the host.  All of it
 // runs on the integer pipes instead of GB300's narrow FP64 pipe.
 //
-// Work split.  Terms are grouped by x-mask (Sec. 3: P|k> pairs k with k^x).
+// Work split.  Terms are grouped by x-mask (Sec. "Multi-qubit rotations in a
+// fullstate simulator": P|k> pairs k with k^x).
 // A thread owns a tile: the coset rep + span(b_0..b_3) of 16 amplitudes,
 // where the basis spans the x-masks of the run and is padded with free index
 // bits.  For an x-mask with coordinates u != 0 in that basis, l and l^u pair
