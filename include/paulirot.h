@@ -280,6 +280,96 @@ int sv_trace_start(sv_state *sv);
  * rows (at most cap; *n_rows = rows written).  Events are recycled. */
 int sv_trace_stop(sv_state *sv, sv_trace_row *rows, int cap, int *n_rows);
 
+/* ---- Clifford-fullstate hybrid: general Clifford frames ------------------------------------ *
+ *
+ * Sec. "Clifford-Fullstate Hybrid Simulator".  A frame F represents a Clifford
+ * unitary U in the backward interpretation, F = U^dag F_origin U (Eq. framemat):
+ * entry j is the pair (U^dag Z_j U, U^dag X_j U), each a Hermitian Pauli string
+ * with a sign.  The pair (F, state) represents psi = U phi (Eq. cfhsstate),
+ * where phi is what the state handle holds (including its own Pauli frame).
+ * Clifford gates only update F on the host; a rotation about P acts on phi
+ * about F(P) = U^dag P U (Eq. single_to_multirot, Eq. Fmap); <P>_psi =
+ * <F(P)>_phi (Eq. chfsexp).  Frames are host objects: the cliff_* calls do no
+ * device work and need no GPU.  n <= 63. */
+typedef struct sv_cliff sv_cliff; /* opaque: 2n signed Pauli strings */
+
+/* Gate codes of a gate stream.  One-qubit gates use q0; CNOT (control q0,
+ * target q1), CZ and SWAP use q0 and q1 (distinct).  RX/RY/RZ(q0, theta) =
+ * exp(-i theta/2 sigma_q0) are the non-Clifford gates: they change the state,
+ * not the frame. */
+#define SV_CG_H 0
+#define SV_CG_S 1   /* diag(1, i) */
+#define SV_CG_SDG 2 /* diag(1, -i) */
+#define SV_CG_X 3
+#define SV_CG_Y 4
+#define SV_CG_Z 5
+#define SV_CG_CNOT 6
+#define SV_CG_CZ 7
+#define SV_CG_SWAP 8
+#define SV_CG_RX 9
+#define SV_CG_RY 10
+#define SV_CG_RZ 11
+
+/* Create an origin frame (U = I) on n qubits.  *out is owned by the caller and
+ * released by cliff_free. */
+int cliff_create(sv_cliff **out, int n_qubits);
+int cliff_free(sv_cliff *f);
+int cliff_reset(sv_cliff *f); /* back to the origin frame */
+int cliff_num_qubits(const sv_cliff *f, int *out);
+
+/* Apply a gate stream to the frame.  Clifford gates update F (each new entry a
+ * product of old entries: U' = g U, F'(P) = F(g^dag P g)); each RX/RY/RZ gate
+ * appends, in order, the rotation phi must undergo: masks of F(sigma_q0) and
+ * the angle times its sign, to out_x/out_z/out_theta (capacity cap; *out_count
+ * = rotations written).  The whole stream (gate codes, qubits, finite angles,
+ * capacity) is checked first: SV_EINVAL leaves the frame unchanged.  gate, q0
+ * are arrays of count; q1 may be NULL if no two-qubit gate occurs, theta if no
+ * rotation gate occurs. */
+int cliff_apply_gates(sv_cliff *f, const int *gate, const int *q0, const int *q1, const double *theta, size_t count,
+                      uint64_t *out_x, uint64_t *out_z, double *out_theta, size_t cap, size_t *out_count);
+
+/* F(P_k) = out_sign[k] * (string with masks out_x[k], out_z[k]) for the
+ * Hermitian strings P_k = (x[k], z[k]) (Eq. Fmap).  Bits >= n: SV_EINVAL. */
+int cliff_map_paulis(const sv_cliff *f, const uint64_t *x, const uint64_t *z, size_t count, uint64_t *out_x,
+                     uint64_t *out_z, int *out_sign);
+
+/* Entry `qubit` of F: U^dag Z_q U = ez_sign * (ez_x, ez_z) and
+ * U^dag X_q U = ex_sign * (ex_x, ex_z). */
+int cliff_entry(const sv_cliff *f, int qubit, uint64_t *ez_x, uint64_t *ez_z, int *ez_sign, uint64_t *ex_x,
+                uint64_t *ex_z, int *ex_sign);
+
+/* *out = 1 if F is the origin frame (U proportional to I), else 0. */
+int cliff_is_origin(const sv_cliff *f, int *out);
+
+/* Rotations R_1..R_m, R_k = exp(-i theta_k/2 P_k) with theta_k = +-pi/2 (that is
+ * exp(-i pi/4 Q_k) for a signed Pauli Q_k), such that U = R_m ... R_1 up to a
+ * global phase: applying R_1 first, then R_2, ... to phi gives U phi (App.
+ * "Efficiently implementing Clifford unitaries with multi-qubit rotations";
+ * construction in csrc/clifford.cu).  m <= 4n; cap >= 4n always suffices. */
+int cliff_inverse_rotations(const sv_cliff *f, uint64_t *out_x, uint64_t *out_z, double *out_theta, size_t cap,
+                            size_t *out_count);
+
+/* Gate stream on (F, sv): Clifford gates update F, the rotation gates run on
+ * sv's amplitudes through apply_pauli_rotations (one plan for the stream).
+ * The frame and the state must have the same n. */
+int cfhs_apply_gates(sv_state *sv, sv_cliff *f, const int *gate, const int *q0, const int *q1, const double *theta,
+                     size_t count);
+
+/* Multi-qubit rotations exp(-i theta_k/2 P_k) applied to psi = U phi: each
+ * runs on sv about F(P_k) with its sign folded into the angle. */
+int cfhs_apply_rotations(sv_state *sv, const sv_cliff *f, const uint64_t *x, const uint64_t *z, const double *theta,
+                         size_t count);
+
+/* <psi| sum_k c_k P_k |psi> = sum_k c_k <phi|F(P_k)|phi> (Eq. chfsexp), with the
+ * reductions of expval_pauli_sum; *out_norm2 (nullable) = <phi|phi>. */
+int cfhs_expval(sv_state *sv, const sv_cliff *f, const uint64_t *x, const uint64_t *z, const double *coeff,
+                size_t count, double *out_energy, double *out_norm2);
+
+/* Apply U to sv's amplitudes (the rotations of cliff_inverse_rotations) and
+ * reset F to the origin frame, so that sv alone holds psi -- up to a global
+ * phase, which a Clifford frame does not fix. */
+int cfhs_materialize(sv_state *sv, sv_cliff *f);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,6 +90,19 @@ def lib() -> ctypes.CDLL:
         "batch_info": ([P(i), P(i), P(i)], i),
         "sv_trace_start": ([vp], i),
         "sv_trace_stop": ([vp, vp, i, P(i)], i),
+        "cliff_create": ([P(vp), i], i),
+        "cliff_free": ([vp], i),
+        "cliff_reset": ([vp], i),
+        "cliff_num_qubits": ([vp, P(i)], i),
+        "cliff_apply_gates": ([vp, vp, vp, vp, vp, sz, vp, vp, vp, sz, P(sz)], i),
+        "cliff_map_paulis": ([vp, vp, vp, sz, vp, vp, vp], i),
+        "cliff_entry": ([vp, i, P(u64), P(u64), P(i), P(u64), P(u64), P(i)], i),
+        "cliff_is_origin": ([vp, P(i)], i),
+        "cliff_inverse_rotations": ([vp, vp, vp, vp, sz, P(sz)], i),
+        "cfhs_apply_gates": ([vp, vp, vp, vp, vp, vp, sz], i),
+        "cfhs_apply_rotations": ([vp, vp, vp, vp, vp, sz], i),
+        "cfhs_expval": ([vp, vp, vp, vp, vp, sz, P(d), P(d)], i),
+        "cfhs_materialize": ([vp, vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -106,7 +119,9 @@ def exported_symbols() -> Sequence[str]:
             "apply_pauli_rotations", "plan_create", "plan_apply", "plan_free", "plan_stats",
             "trotter_expand", "expval_pauli_sum", "expval_pauli_sum_noalloc", "apply_pauli_sum", "rotation_grads",
             "apply_pauli_rotations_gates", "batch_run", "batch_run_ex", "batch_info", "sv_trace_start",
-            "sv_trace_stop"]
+            "sv_trace_stop", "cliff_create", "cliff_free", "cliff_reset", "cliff_num_qubits", "cliff_apply_gates",
+            "cliff_map_paulis", "cliff_entry", "cliff_is_origin", "cliff_inverse_rotations", "cfhs_apply_gates",
+            "cfhs_apply_rotations", "cfhs_expval", "cfhs_materialize"]
 
 
 def _check(rc: int) -> None:
@@ -339,3 +354,107 @@ def sv_trace_stop(sv: int) -> dict:
     _check(lib().sv_trace_stop(sv, rows, 64, ctypes.byref(n)))
     return {rows[i].name.decode(): (int(rows[i].launches), float(rows[i].total_ms), float(rows[i].bytes),
                                     float(rows[i].flops)) for i in range(n.value)}
+
+
+# ------------------------------------------------------------------ Clifford-fullstate hybrid
+
+SV_CG = {"h": 0, "s": 1, "sdg": 2, "x": 3, "y": 4, "z": 5, "cnot": 6, "cz": 7, "swap": 8,
+         "rx": 9, "ry": 10, "rz": 11}
+
+
+def _gates(gates):
+    """[(name, q0[, q1][, theta]), ...] -> int32 codes, q0, q1 and float64 theta arrays.
+    One-qubit gates take (name, q); two-qubit (name, q0, q1); rotations (name, q, theta)."""
+    code = np.zeros(len(gates), dtype=np.int32)
+    q0 = np.zeros(len(gates), dtype=np.int32)
+    q1 = np.full(len(gates), -1, dtype=np.int32)
+    th = np.zeros(len(gates), dtype=np.float64)
+    for k, g in enumerate(gates):
+        c = SV_CG[g[0].lower()]
+        code[k], q0[k] = c, g[1]
+        if c in (6, 7, 8):
+            q1[k] = g[2]
+        elif c >= 9:
+            th[k] = g[2]
+    return code, q0, q1, th
+
+
+def cliff_create(n_qubits: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().cliff_create(ctypes.byref(h), n_qubits))
+    return h.value
+
+
+def cliff_free(f: int) -> None:
+    _check(lib().cliff_free(f))
+
+
+def cliff_reset(f: int) -> None:
+    _check(lib().cliff_reset(f))
+
+
+def cliff_num_qubits(f: int) -> int:
+    n = ctypes.c_int()
+    _check(lib().cliff_num_qubits(f, ctypes.byref(n)))
+    return n.value
+
+
+def cliff_apply_gates(f: int, gates) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Returns the rotations (x, z, theta) the state must undergo, in order."""
+    code, q0, q1, th = _gates(gates)
+    cap = int(np.count_nonzero(code >= 9))
+    ox, oz, ot = np.zeros(cap, np.uint64), np.zeros(cap, np.uint64), np.zeros(cap, np.float64)
+    cnt = ctypes.c_size_t()
+    _check(lib().cliff_apply_gates(f, _p(code), _p(q0), _p(q1), _p(th), len(code), _p(ox), _p(oz), _p(ot), cap,
+                                   ctypes.byref(cnt)))
+    return ox[:cnt.value], oz[:cnt.value], ot[:cnt.value]
+
+
+def cliff_map_paulis(f: int, x, z) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    x, z = _u64(x), _u64(z)
+    ox, oz = np.zeros(x.size, np.uint64), np.zeros(x.size, np.uint64)
+    sg = np.zeros(x.size, np.int32)
+    _check(lib().cliff_map_paulis(f, _p(x), _p(z), x.size, _p(ox), _p(oz), _p(sg)))
+    return ox, oz, sg
+
+
+def cliff_entry(f: int, qubit: int):
+    """((ez_x, ez_z, ez_sign), (ex_x, ex_z, ex_sign)) of entry `qubit`."""
+    v = [ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int()]
+    _check(lib().cliff_entry(f, qubit, *[ctypes.byref(a) for a in v]))
+    return (v[0].value, v[1].value, v[2].value), (v[3].value, v[4].value, v[5].value)
+
+
+def cliff_is_origin(f: int) -> bool:
+    o = ctypes.c_int()
+    _check(lib().cliff_is_origin(f, ctypes.byref(o)))
+    return bool(o.value)
+
+
+def cliff_inverse_rotations(f: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    cap = 4 * cliff_num_qubits(f)
+    ox, oz, ot = np.zeros(cap, np.uint64), np.zeros(cap, np.uint64), np.zeros(cap, np.float64)
+    cnt = ctypes.c_size_t()
+    _check(lib().cliff_inverse_rotations(f, _p(ox), _p(oz), _p(ot), cap, ctypes.byref(cnt)))
+    return ox[:cnt.value], oz[:cnt.value], ot[:cnt.value]
+
+
+def cfhs_apply_gates(sv: int, f: int, gates) -> None:
+    code, q0, q1, th = _gates(gates)
+    _check(lib().cfhs_apply_gates(sv, f, _p(code), _p(q0), _p(q1), _p(th), len(code)))
+
+
+def cfhs_apply_rotations(sv: int, f: int, x, z, angles) -> None:
+    x, z, t = _u64(x), _u64(z), _f64(angles)
+    _check(lib().cfhs_apply_rotations(sv, f, _p(x), _p(z), _p(t), t.size))
+
+
+def cfhs_expval(sv: int, f: int, x, z, coeff) -> Tuple[float, float]:
+    x, z, c = _u64(x), _u64(z), _f64(coeff)
+    e, nrm = ctypes.c_double(), ctypes.c_double()
+    _check(lib().cfhs_expval(sv, f, _p(x), _p(z), _p(c), c.size, ctypes.byref(e), ctypes.byref(nrm)))
+    return e.value, nrm.value
+
+
+def cfhs_materialize(sv: int, f: int) -> None:
+    _check(lib().cfhs_materialize(sv, f))
