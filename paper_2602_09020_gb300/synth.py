@@ -19,6 +19,7 @@ s_p Z..Z s_q s_r Z..Z s_s) with seeded coefficients.
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass, field
 from typing import List, Tuple
 
@@ -260,6 +261,35 @@ def jw_hamiltonian(n: int, n_terms: int, seed: int, *, sigma: float = 0.5,
         emit(x, z, g.normal(0.0, sigma), kind)
         tail -= 1
     return _finish(n, xs, zs, cs, kinds)
+
+
+def random_klocal_hamiltonian(n: int, n_terms: int, k: int, seed: int) -> PauliSum:
+    """Random k-local Hamiltonian of the paper's locality study (Sec. "Evaluation
+    on Random Hamiltonians"): n_terms distinct strings of Pauli weight exactly k,
+    each drawn uniformly from the C(n, k) 3^k such strings, coefficients
+    U[-1, 1] divided by their L1 norm."""
+    if not 1 <= k <= n:
+        raise ValueError(f"locality {k} out of range 1..{n}")
+    if n_terms > math.comb(n, k) * 3 ** k:
+        raise ValueError(f"only {math.comb(n, k) * 3 ** k} distinct strings of weight {k} on {n} qubits")
+    g = _rng(seed)
+    seen, xs, zs = set(), [], []
+    while len(xs) < n_terms:
+        x = z = 0
+        for q in g.choice(n, size=k, replace=False):
+            p = int(g.integers(3))  # 0 = X, 1 = Y, 2 = Z
+            if p < 2:
+                x |= 1 << int(q)
+            if p > 0:
+                z |= 1 << int(q)
+        if (x, z) in seen:
+            continue
+        seen.add((x, z))
+        xs.append(x)
+        zs.append(z)
+    c = g.uniform(-1.0, 1.0, size=n_terms)
+    c = c / np.abs(c).sum()
+    return PauliSum(n, np.array(xs, dtype=np.uint64), np.array(zs, dtype=np.uint64), c, [f"w{k}"] * n_terms)
 
 
 def hartree_fock_index(n_electrons: int) -> int:

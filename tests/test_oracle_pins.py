@@ -327,3 +327,20 @@ def test_generators_are_seeded_and_well_formed():
     assert 10.5 < L.mean() < 12.5 and 4.0 < L.std() < 6.0
     circ = synth.small_workload(0)
     assert len(circ.ham) == 60 and len(circ.gates) == 5 and circ.basis_state == 0b11111
+
+
+def test_random_klocal_generator():
+    """Sec. "Evaluation on Random Hamiltonians": distinct strings of weight exactly
+    k, coefficients of L1 norm 1, seeded."""
+    for k in (2, 4, 12, 24):
+        h = synth.random_klocal_hamiltonian(24, 100, k, seed=5)
+        assert len(h) == 100 and len(set(zip(h.x.tolist(), h.z.tolist()))) == 100
+        assert set(synth.locality(h.x, h.z).tolist()) == {k}
+        assert abs(np.abs(h.c).sum() - 1.0) < 1e-12
+        assert int(np.max(h.x | h.z)) < (1 << 24)
+        g = synth.random_klocal_hamiltonian(24, 100, k, seed=5)
+        assert np.array_equal(h.x, g.x) and np.array_equal(h.z, g.z) and np.array_equal(h.c, g.c)
+    assert len(synth.random_klocal_hamiltonian(24, 72, 1, seed=5)) == 72  # every weight-1 string
+    for args in ((8, 10, 9), (24, 73, 1)):  # k > n; more strings than exist
+        with pytest.raises(ValueError):
+            synth.random_klocal_hamiltonian(*args, seed=0)
