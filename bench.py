@@ -353,6 +353,7 @@ def run_ours(a):
     # batched independent states: one persistent launch vs one launch per pass per state
     if not a.skip_extras:
         extras["batched"] = batch_measure(capi, torch, stream, sh, barrier)
+        extras["locality_sweep"] = locality_measure(capi, torch, a.n, a.dtype, barrier)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -421,6 +422,44 @@ def run_ours(a):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def locality_measure(capi, torch, n: int, dtype: str, barrier, terms: int = 100,
+                     localities=(4, 8, 12, 16, 20, 24)):
+    """The paper's locality study (Sec. "Evaluation on Random Hamiltonians"): one
+    first-order Trotter step of a random k-local Hamiltonian with 100 terms at
+    each locality L, run as fused rotations and gate-decomposed on the same GPU.
+    Device time (CUDA events on the states' stream); the fused path should be
+    flat in L, the gate path linear in L."""
+    own = torch.cuda.Stream()
+    sh = int(own.cuda_stream)
+    rows = []
+    for L in localities:
+        if L > n:
+            continue
+        ham = synth.random_klocal_hamiltonian(n, terms, L, seed=1000 + L)
+        rx, rz, rt = capi.trotter_expand(ham.x, ham.z, ham.c, 1.0, 1, 1, False)
+        sv = capi.sv_alloc(n, dtype, sh)
+        capi.sv_set_basis_state(sv, 0)
+        plan = capi.plan_create(n, dtype, rx, rz, rt, -1, sh)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        capi.plan_apply(sv, plan)  # warm both paths
+        capi.apply_pauli_rotations_gates(sv, rx[:2], rz[:2], rt[:2])
+        barrier()
+        e[0].record(own)
+        capi.plan_apply(sv, plan)
+        e[1].record(own)
+        e[2].record(own)
+        ngates = capi.apply_pauli_rotations_gates(sv, rx, rz, rt)
+        e[3].record(own)
+        barrier()
+        fused_ms, gate_ms = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+        passes = capi.plan_stats(plan)[1]
+        capi.plan_free(plan)
+        capi.sv_free(sv)
+        rows.append({"L": L, "rotations": len(rt), "fused_ms": fused_ms, "fused_passes": passes,
+                     "gates": ngates, "gate_ms": gate_ms, "speedup": gate_ms / fused_ms})
+    return {"n": n, "terms": terms, "dtype": dtype, "rows": rows}
 
 
 def batch_measure(capi, torch, stream, sh, barrier, reps: int = 3):
