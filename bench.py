@@ -354,6 +354,8 @@ def run_ours(a):
     if not a.skip_extras:
         extras["batched"] = batch_measure(capi, torch, stream, sh, barrier)
         extras["locality_sweep"] = locality_measure(capi, torch, a.n, a.dtype, barrier)
+        extras["cfhs_gate_stream"] = cfhs_measure(capi, torch, a.n, a.dtype, rx[:a.terms], rz[:a.terms],
+                                                  rt[:a.terms], ham, basis, barrier)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -394,6 +396,14 @@ def run_ours(a):
         rate, k, threads, el = oracle_rate(a.n, rx, rz, rt, 12.0, basis)
         cpu = {"value": rate, "unit": "rotations/s", "cores": threads, "kind": "oracle",
                "sample": f"first {k} rotations of the step at n={a.n}, complex128 gate-decomposed ({el:.1f} s)"}
+        import oracle
+        oracle.set_num_threads(1)
+        try:
+            rate1, k1, _, el1 = oracle_rate(a.n, rx, rz, rt, 4.0, basis)
+        finally:
+            oracle.set_num_threads(0)
+        cpu["single_thread"] = {"value": rate1, "unit": "rotations/s", "cores": 1,
+                                "sample": f"first {k1} rotations, one thread ({el1:.1f} s)"}
 
     if rank != 0:
         return 0
@@ -460,6 +470,73 @@ def locality_measure(capi, torch, n: int, dtype: str, barrier, terms: int = 100,
         rows.append({"L": L, "rotations": len(rt), "fused_ms": fused_ms, "fused_passes": passes,
                      "gates": ngates, "gate_ms": gate_ms, "speedup": gate_ms / fused_ms})
     return {"n": n, "terms": terms, "dtype": dtype, "rows": rows}
+
+
+def staircase_stream(x: int, z: int, theta: float, out: list) -> None:
+    """Append the textbook gate decomposition of exp(-i theta/2 P) (basis
+    change, CNOT ladder over the support, Rz on its top qubit, undo) as
+    (code, q0, q1, theta) tuples in the SV_CG numbering."""
+    H, S, SDG, CNOT, RZ = 0, 1, 2, 6, 11
+    sup = [q for q in range(64) if ((x | z) >> q) & 1]
+    basis = []
+    for q in sup:
+        if (x >> q) & 1 and (z >> q) & 1:
+            basis += [(SDG, q, -1, 0.0), (H, q, -1, 0.0)]
+        elif (x >> q) & 1:
+            basis.append((H, q, -1, 0.0))
+    ladder = [(CNOT, a, b, 0.0) for a, b in zip(sup, sup[1:])]
+    undo = [((S if g == SDG else g), q, -1, 0.0) for (g, q, _, _) in reversed(basis)]
+    out += basis + ladder + [(RZ, sup[-1], -1, theta)] + ladder[::-1] + undo
+
+
+def cfhs_measure(capi, torch, n: int, dtype: str, rx, rz, rt, ham, basis: int, barrier):
+    """The hybrid simulator's use case (Sec. "Description of the Clifford-fullstate
+    hybrid simulation"): the first Trotter step written out as a gate-level
+    circuit -- every rotation as basis changes, a CNOT ladder, one Rz and the
+    undo -- fed to cfhs_apply_gates.  The Clifford gates only update the host
+    frame; the Rz gates reach the GPU as fused rotations about the frame's Z_q.
+    Wall time around the call (host frame updates, planning and the GPU work);
+    the energy through the frame is compared with the direct rotation path."""
+    stream = []
+    for x, z, t in zip(rx, rz, rt):
+        if int(x) | int(z):
+            staircase_stream(int(x), int(z), float(t), stream)
+    arr = np.array(stream, dtype=np.float64)
+    code = np.ascontiguousarray(arr[:, 0].astype(np.int32))
+    q0 = np.ascontiguousarray(arr[:, 1].astype(np.int32))
+    q1 = np.ascontiguousarray(arr[:, 2].astype(np.int32))
+    th = np.ascontiguousarray(arr[:, 3])
+    own = torch.cuda.Stream()
+    sh = int(own.cuda_stream)
+    lib = capi.lib()
+    sv = capi.sv_alloc(n, dtype, sh)
+    f = capi.cliff_create(n)
+    ref = capi.sv_alloc(n, dtype, sh)
+    try:
+        capi.sv_set_basis_state(sv, basis)
+        capi._check(lib.cfhs_apply_gates(sv, f, code.ctypes.data, q0.ctypes.data, q1.ctypes.data, th.ctypes.data,
+                                         len(code)))  # warm (first launches)
+        capi.cliff_reset(f)
+        capi.sv_set_basis_state(sv, basis)
+        barrier()
+        t0 = time.perf_counter()
+        capi._check(lib.cfhs_apply_gates(sv, f, code.ctypes.data, q0.ctypes.data, q1.ctypes.data, th.ctypes.data,
+                                         len(code)))
+        barrier()
+        wall = time.perf_counter() - t0
+        e_cfhs, _ = capi.cfhs_expval(sv, f, ham.x, ham.z, ham.c)
+        capi.sv_set_basis_state(ref, basis)
+        capi.apply_pauli_rotations(ref, rx, rz, rt)
+        e_ref, _ = capi.expval_pauli_sum(ref, ham.x, ham.z, ham.c)
+    finally:
+        capi.cliff_free(f)
+        capi.sv_free(sv)
+        capi.sv_free(ref)
+    n_rz = int(np.count_nonzero(code == 11))
+    return {"rotations": n_rz, "gates": len(code), "clifford_gates": len(code) - n_rz, "wall_ms": 1000.0 * wall,
+            "rotations_per_s": n_rz / wall, "gates_per_s": len(code) / wall,
+            "energy_through_frame": e_cfhs, "energy_direct": e_ref,
+            "sample": "the first Trotter step as a gate-level circuit"}
 
 
 def batch_measure(capi, torch, stream, sh, barrier, reps: int = 3):

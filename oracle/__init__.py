@@ -35,7 +35,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 __all__ = [
-    "build", "lib", "num_threads", "basis_state", "apply_rotations", "apply_rotation",
+    "build", "lib", "num_threads", "set_num_threads", "basis_state", "apply_rotations", "apply_rotation",
     "apply_pauli", "apply_sequence", "norm2", "inner", "expval", "apply_pauli_sum",
     "trotter_rotations", "circuit_sequence", "run_circuit", "grad_param_shift",
     "rotation_gate_count", "gate",
@@ -78,6 +78,7 @@ def lib() -> ctypes.CDLL:
         L.orc_apply_pauli_sum.argtypes = [cx, ctypes.c_int, vp, vp, vp, i64, cx, cx]
         L.orc_rotation_gate_count.argtypes = [u64, u64, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = L
     return _lib
 
@@ -94,6 +95,11 @@ def _state(psi: np.ndarray, n: int) -> np.ndarray:
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    """Threads for later calls; k <= 0 = one per processor (timing only)."""
+    lib().orc_set_num_threads(int(k))
 
 
 def basis_state(n: int, k: int) -> np.ndarray:

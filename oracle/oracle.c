@@ -51,6 +51,17 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Thread count for later calls (timing only: single-thread and all-core rates
+ * of the same oracle); k <= 0 restores one thread per processor. */
+void orc_set_num_threads(int k)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(k > 0 ? k : omp_get_num_procs());
+#else
+    (void)k;
+#endif
+}
+
 /* ---- one-qubit gates ------------------------------------------------------ */
 
 void orc_gate_x(cx *a, int n, int q)
