@@ -370,6 +370,26 @@ int cfhs_expval(sv_state *sv, const sv_cliff *f, const uint64_t *x, const uint64
  * phase, which a Clifford frame does not fix. */
 int cfhs_materialize(sv_state *sv, sv_cliff *f);
 
+/* Projective measurement of the Hermitian Pauli string P = (x, z) on
+ * psi = U phi (f may be NULL: U = I), App. "Complete workflow of the hybrid
+ * Clifford fullstate simulation" (Meas on the frame-rewritten axis).  The +1
+ * probability is p = (1 + <psi|P|psi>/<psi|psi>)/2, from the reductions of
+ * expval_pauli_sum; the outcome is +1 if u < p, else -1, with u a uniform
+ * number in [0, 1) the caller draws (SV_EINVAL otherwise).  An outcome whose
+ * probability is below 1e-14 is never taken.  The state becomes the
+ * normalised projection (I + outcome P) psi / |(I + outcome P) psi| (one pass
+ * over the amplitudes).  *out_outcome = +-1, *out_prob = its probability
+ * (both nullable). */
+int cfhs_measure_pauli(sv_state *sv, const sv_cliff *f, uint64_t x, uint64_t z, double u, int *out_outcome,
+                       double *out_prob);
+
+/* Prepare `qubit` in the +1 eigenstate of pauli ('X', 'Y' or 'Z') of psi =
+ * U phi (f may be NULL), the workflow's Prep: measure that axis as
+ * cfhs_measure_pauli does (uniform u) and, on outcome -1, apply an
+ * anticommuting partner (Z for X and Y, X for Z) through the frames, so that
+ * no extra pass runs.  *out_outcome (nullable) = the measured outcome. */
+int cfhs_prepare_qubit(sv_state *sv, const sv_cliff *f, int qubit, char pauli, double u, int *out_outcome);
+
 #ifdef __cplusplus
 }
 #endif

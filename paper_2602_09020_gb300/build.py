@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpaulirot.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["state.cu", "plan.cu", "rotate.cu", "reduce.cu", "adjoint.cu", "gates.cu", "batch.cu", "clifford.cu",
+SOURCES = ["state.cu", "plan.cu", "rotate.cu", "reduce.cu", "adjoint.cu", "gates.cu", "batch.cu", "clifford.cu", "measure.cu",
            "trace.cu"]
 
 

@@ -103,6 +103,8 @@ def lib() -> ctypes.CDLL:
         "cfhs_apply_rotations": ([vp, vp, vp, vp, vp, sz], i),
         "cfhs_expval": ([vp, vp, vp, vp, vp, sz, P(d), P(d)], i),
         "cfhs_materialize": ([vp, vp], i),
+        "cfhs_measure_pauli": ([vp, vp, u64, u64, d, P(i), P(d)], i),
+        "cfhs_prepare_qubit": ([vp, vp, i, ctypes.c_char, d, P(i)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -121,7 +123,7 @@ def exported_symbols() -> Sequence[str]:
             "apply_pauli_rotations_gates", "batch_run", "batch_run_ex", "batch_info", "sv_trace_start",
             "sv_trace_stop", "cliff_create", "cliff_free", "cliff_reset", "cliff_num_qubits", "cliff_apply_gates",
             "cliff_map_paulis", "cliff_entry", "cliff_is_origin", "cliff_inverse_rotations", "cfhs_apply_gates",
-            "cfhs_apply_rotations", "cfhs_expval", "cfhs_materialize"]
+            "cfhs_apply_rotations", "cfhs_expval", "cfhs_materialize", "cfhs_measure_pauli", "cfhs_prepare_qubit"]
 
 
 def _check(rc: int) -> None:
@@ -458,3 +460,18 @@ def cfhs_expval(sv: int, f: int, x, z, coeff) -> Tuple[float, float]:
 
 def cfhs_materialize(sv: int, f: int) -> None:
     _check(lib().cfhs_materialize(sv, f))
+
+
+def cfhs_measure_pauli(sv: int, f: Optional[int], x: int, z: int, u: float) -> Tuple[int, float]:
+    """Measure the Pauli (x, z) on the state (through frame f, or None); returns
+    (outcome +-1, its probability).  u: a uniform draw in [0, 1)."""
+    o, p = ctypes.c_int(), ctypes.c_double()
+    _check(lib().cfhs_measure_pauli(sv, f, int(x), int(z), float(u), ctypes.byref(o), ctypes.byref(p)))
+    return o.value, p.value
+
+
+def cfhs_prepare_qubit(sv: int, f: Optional[int], qubit: int, pauli: str, u: float) -> int:
+    """Put `qubit` in the +1 eigenstate of pauli ('X', 'Y', 'Z'); returns the measured outcome."""
+    o = ctypes.c_int()
+    _check(lib().cfhs_prepare_qubit(sv, f, qubit, pauli.encode()[:1], float(u), ctypes.byref(o)))
+    return o.value
