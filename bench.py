@@ -356,6 +356,8 @@ def run_ours(a):
         extras["locality_sweep"] = locality_measure(capi, torch, a.n, a.dtype, barrier)
         extras["cfhs_gate_stream"] = cfhs_measure(capi, torch, a.n, a.dtype, rx[:a.terms], rz[:a.terms],
                                                   rt[:a.terms], ham, basis, barrier)
+        extras["large_state"] = large_measure(capi, torch, barrier)
+        extras["adjoint"] = adjoint_measure(capi, torch, barrier)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -537,6 +539,68 @@ def cfhs_measure(capi, torch, n: int, dtype: str, rx, rz, rt, ham, basis: int, b
             "rotations_per_s": n_rz / wall, "gates_per_s": len(code) / wall,
             "energy_through_frame": e_cfhs, "energy_direct": e_ref,
             "sample": "the first Trotter step as a gate-level circuit"}
+
+
+def large_measure(capi, torch, barrier, n: int = 30, terms: int = 5000, seed: int = 1):
+    """The large-state workload: complex64 at n = 30 (8 GiB), a 5000-term JW-shaped
+    Hamiltonian, one symmetric second-order Trotter step (neighbours merged:
+    9,999 rotations) from the Hartree-Fock state, then <H> and the norm.  Device
+    time of one step after one warm-up step; the norm drift is |<psi|psi> - 1|."""
+    ham = synth.jw_hamiltonian(n, terms, seed)
+    rx, rz, rt = capi.trotter_expand(ham.x, ham.z, ham.c, 0.05, 1, 2, True)
+    own = torch.cuda.Stream()
+    sh = int(own.cuda_stream)
+    plan = capi.plan_create(n, "c64", rx, rz, rt, -1, sh)
+    sv = capi.sv_alloc(n, "c64", sh)
+    basis = synth.hartree_fock_index(n // 2)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    try:
+        capi.sv_set_basis_state(sv, basis)
+        capi.plan_apply(sv, plan)  # warm
+        capi.expval_pauli_sum(sv, ham.x, ham.z, ham.c)
+        capi.sv_set_basis_state(sv, basis)
+        barrier()
+        e0.record(own)
+        capi.plan_apply(sv, plan)
+        e1.record(own)
+        e, nrm = capi.expval_pauli_sum(sv, ham.x, ham.z, ham.c)
+        e2.record(own)
+        barrier()
+        passes = capi.plan_stats(plan)[1]
+    finally:
+        capi.sv_free(sv)
+        capi.plan_free(plan)
+    rot_ms, h_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    return {"n": n, "dtype": "c64", "terms": terms, "rotations": len(rt), "passes": passes,
+            "rotations_ms": rot_ms, "expval_ms": h_ms, "rotations_per_s": len(rt) / (rot_ms / 1000.0),
+            "hbm_fraction_algorithmic": passes * 2.0 * 8 * (1 << n) / (rot_ms / 1000.0) / 1e9 / peaks()["hbm_gbs"],
+            "energy": e, "norm_drift": abs(nrm - 1.0)}
+
+
+def adjoint_measure(capi, torch, barrier, n: int = 20, n_rot: int = 500, n_obs: int = 300):
+    """The gradient workload: E(theta) = <psi(theta)|H|psi(theta)> and all 500
+    dE/dtheta_j at n = 20 by the adjoint sweep (rotation_grads), in both
+    precisions; wall time of one call after a warm-up call."""
+    x, z, th, obs = synth.adjoint_workload(n, n_rot, n_obs, seed=20)
+    basis = synth.hartree_fock_index(n // 2)
+    own = torch.cuda.Stream()
+    sh = int(own.cuda_stream)
+    out = {"n": n, "rotations": n_rot, "observable_terms": n_obs}
+    for dtype in ("c128", "c64"):
+        sv = capi.sv_alloc(n, dtype, sh)
+        try:
+            capi.sv_set_basis_state(sv, basis)
+            capi.rotation_grads(sv, x, z, th, obs.x, obs.z, obs.c)  # warm
+            barrier()
+            t0 = time.perf_counter()
+            e, g = capi.rotation_grads(sv, x, z, th, obs.x, obs.z, obs.c)
+            barrier()
+            el = time.perf_counter() - t0
+        finally:
+            capi.sv_free(sv)
+        out[dtype] = {"ms": 1000.0 * el, "gradients_per_s": n_rot / el, "energy": e,
+                      "max_abs_grad": float(np.abs(g).max())}
+    return out
 
 
 def batch_measure(capi, torch, stream, sh, barrier, reps: int = 3):
