@@ -417,8 +417,13 @@ __host__ __device__ constexpr size_t ws_c64x2() {
 template <typename Idx, int D>
 __device__ __forceinline__ void body_c64x2(float4 *__restrict__ amp4, Idx n_pairs, const RunDev &run,
                                            const RotDev *__restrict__ rots, uint64_t fx, uint64_t fz,
-                                           Idx cta_rank, Idx cta_count, char *ws) {
+                                           Idx cta_rank, Idx cta_count, char *ws, bool chained = false) {
   constexpr int E = 1 << D;
+  // chained: launched as a programmatic dependent of the previous pass.  The
+  // next pass may be scheduled as this one's CTAs retire; this pass reads its
+  // rotation table before waiting for the previous pass, and touches no
+  // amplitude until that pass has completed and its writes are visible.
+  if (chained) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   RotSm2<Idx> *srot = (RotSm2<Idx> *)ws;
   Idx *soff = (Idx *)(ws + sizeof(RotSm2<Idx>) * kMaxRunRots);
   float4 *stage = (float4 *)(ws + ws_c64x2_head<Idx, D>());
@@ -446,6 +451,7 @@ __device__ __forceinline__ void body_c64x2(float4 *__restrict__ amp4, Idx n_pair
     soff[threadIdx.x] = (Idx)s;
   }
   __syncthreads();
+  if (chained) asm volatile("griddepcontrol.wait;" ::: "memory");
 
   const Idx stride = cta_count * blockDim.x;
   float4 *slot = stage + threadIdx.x;

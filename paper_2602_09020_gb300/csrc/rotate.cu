@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kThreads)
     k_coset_c64x2(float4 *__restrict__ amp4, Idx n_pairs, const __grid_constant__ RunDev run, const RotDev *__restrict__ rots,
                   uint64_t fx, uint64_t fz) {
   extern __shared__ __align__(16) char dyn_ws[];
-  body_c64x2<Idx, D>(amp4, n_pairs, run, rots, fx, fz, (Idx)blockIdx.x, (Idx)gridDim.x, dyn_ws);
+  body_c64x2<Idx, D>(amp4, n_pairs, run, rots, fx, fz, (Idx)blockIdx.x, (Idx)gridDim.x, dyn_ws, true);
 }
 
 template <typename R, typename Idx>
@@ -102,9 +102,22 @@ int launch_c64x2_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_
   unsigned blocks = (unsigned)(need < (uint64_t)cap ? need : (uint64_t)cap);
   if (!blocks) blocks = 1;
   const int tr = trace_begin(sv);
-  k_coset_c64x2<Idx, D><<<blocks, kThreads, dyn, sv->stream>>>((float4 *)sv->amps, (Idx)n_pairs, run,
-                                                               plan->d_rots, fx, fz);
-  PR_CHECK_LAUNCH();
+  // programmatic dependent launch: the grid never exceeds what the GPU holds at
+  // once, so the early-scheduled CTAs of this pass cannot keep the previous
+  // pass's CTAs from running, and each waits for that pass before touching
+  // amplitudes (griddepcontrol.wait in body_c64x2)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = sv->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  PR_CUDA(cudaLaunchKernelEx(&cfg, k_coset_c64x2<Idx, D>, (float4 *)sv->amps, (Idx)n_pairs, run,
+                             (const RotDev *)plan->d_rots, fx, fz));
   trace_end(sv, tr, KN_COSET0 + D, 2.0 * 8.0 * (double)(1ULL << sv->n),
             4.0 * (double)run.count * (double)(1ULL << sv->n));
   return SV_OK;
