@@ -190,3 +190,28 @@ def test_rejected_streams_leave_the_frame():
             capi.cliff_map_paulis(f, [8], [0])  # bit at n
     finally:
         capi.cliff_free(f)
+
+
+def test_bench_gate_stream_reproduces_the_rotations():
+    """The gate-level circuit bench.py feeds to the hybrid path (every rotation as
+    basis changes, CNOT ladder, Rz, undo) emits exactly the original rotations
+    and leaves the frame at the origin."""
+    import bench
+    from paper_2602_09020_gb300 import synth
+
+    ham = synth.jw_hamiltonian(12, 60, 3)
+    stream = []
+    for x, z, c in zip(ham.x, ham.z, ham.c):
+        bench.staircase_stream(int(x), int(z), 2 * float(c), stream)
+    names = {0: "h", 1: "s", 2: "sdg", 6: "cnot", 11: "rz"}
+    gates = [(names[g], q0, q1) if g == 6 else (names[g], q0, t) if g == 11 else (names[g], q0)
+             for g, q0, q1, t in stream]
+    f = capi.cliff_create(12)
+    try:
+        ox, oz, ot = capi.cliff_apply_gates(f, gates)
+        assert capi.cliff_is_origin(f)
+    finally:
+        capi.cliff_free(f)
+    keep = (ham.x | ham.z) != 0
+    assert np.array_equal(ox, ham.x[keep]) and np.array_equal(oz, ham.z[keep])
+    np.testing.assert_array_equal(ot, 2 * ham.c[keep])
