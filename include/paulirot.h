@@ -210,8 +210,11 @@ int apply_pauli_sum(sv_state *dst, sv_state *src, const uint64_t *x, const uint6
 /* E = <psi|H|psi> with psi = R_{n_rot-1} ... R_0 psi0 (psi0 = the represented
  * state of the handle, left unchanged), and out_grads[j] = dE/dtheta_j for all
  * j, FP64.  Adjoint method: lambda = H psi, then for j = n_rot-1 .. 0:
- * g_j = Im <lambda|P_j|phi_j>, phi <- R_j^dag phi, lambda <- R_j^dag lambda.
- * Uses two temporary states of psi0's size. */
+ * g_j = Im <lambda|P_j|phi_j>, phi <- R_j^dag phi, lambda <- R_j^dag lambda,
+ * walked in fused runs (consecutive rotations whose x-masks span <= 3
+ * dimensions share one pass over phi and lambda).  The two work states (phi,
+ * lambda; psi0's size and type) are allocated on the first call, kept on psi0's
+ * handle for later calls and released by sv_free(psi0). */
 int rotation_grads(sv_state *psi0, const uint64_t *x, const uint64_t *z, const double *angles,
                    size_t n_rot, const uint64_t *hx, const uint64_t *hz, const double *hc,
                    size_t n_terms, double *out_energy, double *out_grads);

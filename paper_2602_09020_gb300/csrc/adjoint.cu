@@ -8,6 +8,7 @@
 // +-P_j with the applied (reduced) angle beta_j; the gradient picks up the
 // same frame sign (see plan.cu for the reduction).
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "internal.h"
@@ -109,6 +110,174 @@ __global__ void __launch_bounds__(kThreads)
   if (threadIdx.x == 0) partials[blockIdx.x] = g;
 }
 
+// ---- fused backward runs ------------------------------------------------------
+//
+// Im<lambda|P|phi> is a sum over amplitudes, and P pairs k with k^x inside any
+// coset of a subspace that contains x.  So a run of consecutive rotations whose
+// x-masks span <= kAdjD dimensions is walked backwards coset by coset: a thread
+// keeps one coset of phi and of lambda in FP64 registers and, for each rotation
+// of the run (latest first), adds the coset's share of Im<lambda|P_j|phi> to a
+// per-rotation accumulator, then applies R_j^dag = c + i s P_j to both.  One
+// read and one write of phi and lambda per run instead of per rotation; the
+// arithmetic per rotation is that of k_adjoint_step.
+
+constexpr int kAdjD = 3;     // run span dimension: 8 elements per coset
+constexpr int kAdjRun = 20;  // rotations per run (shared-memory accumulators)
+
+struct AdjRotDev {
+  uint64_t z;
+  double c, s;   // R(-beta) = c + i s P
+  int32_t u;     // coordinates of x in the run basis
+  int32_t ny;    // popc(x & z) mod 4
+  uint32_t zt;   // bit e = parity(soff[e] & z)
+  int32_t row;   // gradient row (plan order)
+};
+struct AdjRunDev {
+  uint64_t soff[1 << kAdjD];
+  int32_t piv[kAdjD];  // ascending
+  int32_t count;
+  AdjRotDev rot[kAdjRun];  // backward order
+};
+
+__host__ __device__ constexpr int adj_high_bit(int v) {
+  int h = 0;
+  while (v >> (h + 1)) ++h;
+  return h;
+}
+
+__device__ __forceinline__ double im_conj_mul(double2 a, double2 b) { return a.x * b.y - a.y * b.x; }  // Im(conj(a) b)
+
+// i^K v, by swaps and negations
+template <int K>
+__device__ __forceinline__ double2 ipow(double2 v) {
+  if constexpr ((K & 3) == 0) return v;
+  if constexpr ((K & 3) == 1) return make_double2(-v.y, v.x);
+  if constexpr ((K & 3) == 2) return make_double2(-v.x, -v.y);
+  return make_double2(v.y, -v.x);
+}
+
+// Im(conj(a) i^K b)
+template <int K>
+__device__ __forceinline__ double im_conj_ipow(double2 a, double2 b) {
+  if constexpr ((K & 3) == 0) return a.x * b.y - a.y * b.x;
+  if constexpr ((K & 3) == 1) return a.x * b.x + a.y * b.y;
+  if constexpr ((K & 3) == 2) return a.y * b.x - a.x * b.y;
+  return -(a.x * b.x + a.y * b.y);
+}
+
+// One rotation on a coset, U = pairing pattern, K = nY mod 4.  With
+// (P v)_e = i^K (-1)^{sigma_m} v_m for the partner m = e ^ U:
+//   g   += (-1)^{sigma_m} Im(conj(lambda_e) i^K phi_m) + (e <-> m),
+//   v_e <- c v_e + s (-1)^{sigma_m} i^{K+1} v_m     (R^dag = c + i s P),
+// so the phase costs swaps and negations only.
+template <int U, int K>
+__device__ __forceinline__ void adj_rot(double2 (&p)[1 << kAdjD], double2 (&l)[1 << kAdjD], const AdjRotDev &r,
+                                        int sig, double &g) {
+  constexpr int E = 1 << kAdjD;
+  const double c = r.c, s = r.s;
+  if constexpr (U == 0) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const bool neg = (sig ^ (int)(r.zt >> e)) & 1;
+      const double ss = neg ? -s : s;
+      const double2 pe = p[e], le = l[e];
+      const double ge = im_conj_mul(le, pe);
+      g += neg ? -ge : ge;
+      p[e] = make_double2(c * pe.x - ss * pe.y, c * pe.y + ss * pe.x);
+      l[e] = make_double2(c * le.x - ss * le.y, c * le.y + ss * le.x);
+    }
+  } else {
+    constexpr int H = adj_high_bit(U);
+#pragma unroll
+    for (int q = 0; q < E / 2; ++q) {
+      const int e = ((q >> H) << (H + 1)) | (q & ((1 << H) - 1));
+      const int m = e ^ U;
+      const bool ne = (sig ^ (int)(r.zt >> e)) & 1, nm = (sig ^ (int)(r.zt >> m)) & 1;
+      const double2 pe = p[e], pm = p[m], le = l[e], lm = l[m];
+      const double ge = im_conj_ipow<K>(le, pm), gm = im_conj_ipow<K>(lm, pe);
+      g += (nm ? -ge : ge) + (ne ? -gm : gm);
+      const double se = ne ? -s : s, sm = nm ? -s : s;
+      const double2 wpm = ipow<K + 1>(pm), wpe = ipow<K + 1>(pe), wlm = ipow<K + 1>(lm), wle = ipow<K + 1>(le);
+      p[e] = make_double2(c * pe.x + sm * wpm.x, c * pe.y + sm * wpm.y);
+      p[m] = make_double2(c * pm.x + se * wpe.x, c * pm.y + se * wpe.y);
+      l[e] = make_double2(c * le.x + sm * wlm.x, c * le.y + sm * wlm.y);
+      l[m] = make_double2(c * lm.x + se * wle.x, c * lm.y + se * wle.y);
+    }
+  }
+}
+
+#define PR_ADJ_CASE(UK) \
+  case UK: adj_rot<((UK) >> 2), ((UK)&3)>(p, l, r, sig, g); break;
+
+__device__ __forceinline__ void adj_dispatch(int uk, double2 (&p)[1 << kAdjD], double2 (&l)[1 << kAdjD],
+                                             const AdjRotDev &r, int sig, double &g) {
+  switch (uk) {
+    PR_ADJ_CASE(0)
+    PR_ADJ_CASE(4) PR_ADJ_CASE(5) PR_ADJ_CASE(6) PR_ADJ_CASE(7)
+    PR_ADJ_CASE(8) PR_ADJ_CASE(9) PR_ADJ_CASE(10) PR_ADJ_CASE(11)
+    PR_ADJ_CASE(12) PR_ADJ_CASE(13) PR_ADJ_CASE(14) PR_ADJ_CASE(15)
+    PR_ADJ_CASE(16) PR_ADJ_CASE(17) PR_ADJ_CASE(18) PR_ADJ_CASE(19)
+    PR_ADJ_CASE(20) PR_ADJ_CASE(21) PR_ADJ_CASE(22) PR_ADJ_CASE(23)
+    PR_ADJ_CASE(24) PR_ADJ_CASE(25) PR_ADJ_CASE(26) PR_ADJ_CASE(27)
+    PR_ADJ_CASE(28) PR_ADJ_CASE(29) PR_ADJ_CASE(30) PR_ADJ_CASE(31)
+    default: break;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    k_adjoint_run(typename Cx<R>::T *__restrict__ phi, typename Cx<R>::T *__restrict__ lam, uint64_t n_cosets,
+                  const __grid_constant__ AdjRunDev run, int row_stride, double *__restrict__ partials) {
+  using C = typename Cx<R>::T;
+  constexpr int E = 1 << kAdjD;
+  __shared__ double sacc[kAdjRun][kThreads];  // one column per thread
+  for (int j = 0; j < kAdjRun; ++j) sacc[j][threadIdx.x] = 0.0;
+  const int count = run.count;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t cs = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; cs < n_cosets; cs += stride) {
+    uint64_t rep = cs;
+#pragma unroll
+    for (int b = 0; b < kAdjD; ++b) {
+      const int pv = run.piv[b];
+      rep = ((rep >> pv) << (pv + 1)) | (rep & ((1ULL << pv) - 1));
+    }
+    double2 p[E], l[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const C pv = phi[rep ^ run.soff[e]], lv = lam[rep ^ run.soff[e]];
+      p[e] = make_double2(pv.x, pv.y);
+      l[e] = make_double2(lv.x, lv.y);
+    }
+    for (int j = 0; j < count; ++j) {
+      const AdjRotDev &r = run.rot[j];
+      const int sig = __popcll(rep & r.z) & 1;
+      double g = 0.0;
+      adj_dispatch(r.u * 4 + r.ny, p, l, r, sig, g);  // x = 0 has nY = 0
+      sacc[j][threadIdx.x] += g;
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      C o;
+      o.x = (R)p[e].x;
+      o.y = (R)p[e].y;
+      phi[rep ^ run.soff[e]] = o;
+      o.x = (R)l[e].x;
+      o.y = (R)l[e].y;
+      lam[rep ^ run.soff[e]] = o;
+    }
+  }
+  __syncthreads();
+  // block sums in a fixed order: warp w reduces rows w, w + 8, ...
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = w; j < count; j += (int)(blockDim.x >> 5)) {
+    double v = 0.0;
+    for (int i = lane; i < (int)blockDim.x; i += 32) v += sacc[j][i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) partials[(size_t)run.rot[j].row * row_stride + blockIdx.x] = v;
+  }
+}
+
 __global__ void k_sum_rows(const double *__restrict__ partials, int n_blocks, double *__restrict__ out) {
   const double *p = partials + (size_t)blockIdx.x * n_blocks;
   double a = 0.0;
@@ -123,6 +292,118 @@ int step_blocks(int n) {
   uint64_t cap = (uint64_t)device_sm_count() * 4;
   uint64_t b = need < cap ? need : cap;
   return b ? (int)b : 1;
+}
+
+template <typename R>
+int run_blocks_t(int n) {
+  static int cap = 0;
+  if (!cap) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_run<R>, kThreads, 0) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    cap = (per_sm > 0 ? per_sm : 1) * device_sm_count();
+  }
+  const uint64_t need = (((1ULL << n) >> kAdjD) + kThreads - 1) / kThreads;
+  return (int)(need < (uint64_t)cap ? (need ? need : 1) : cap);
+}
+
+int run_blocks(const sv_state *sv) { return sv->dtype == SV_C128 ? run_blocks_t<double>(sv->n) : run_blocks_t<float>(sv->n); }
+
+// The backward sweep as fused runs: rotations in applied order L-1 .. 0, grouped
+// greedily into runs of <= kAdjRun whose x-masks span <= kAdjD dimensions.
+// Identity strings change only a global phase of both vectors (skipped); their
+// gradient rows stay zero.
+int adjoint_runs(sv_state *phi, sv_state *lam, const sv_plan *plan, const Pauli &q0, int blocks) {
+  const size_t L = plan->order.size();
+  PR_CUDA(cudaMemsetAsync(phi->d_partials, 0, sizeof(double) * (size_t)blocks * L, phi->stream));
+  const uint64_t n_cosets = (1ULL << phi->n) >> kAdjD;
+  size_t i = L;
+  while (i > 0) {
+    uint64_t basis[kAdjD];
+    int piv[kAdjD];
+    int d = 0;
+    auto reduce = [&](uint64_t v) {
+      for (int b = 0; b < d; ++b)
+        if ((v >> piv[b]) & 1ULL) v ^= basis[b];
+      return v;
+    };
+    auto add_vec = [&](uint64_t rr) {
+      const int pv = 63 - __builtin_clzll(rr);
+      for (int b = 0; b < d; ++b)
+        if ((basis[b] >> pv) & 1ULL) basis[b] ^= rr;
+      int pos = d;
+      while (pos > 0 && piv[pos - 1] > pv) {
+        basis[pos] = basis[pos - 1];
+        piv[pos] = piv[pos - 1];
+        --pos;
+      }
+      basis[pos] = rr;
+      piv[pos] = pv;
+      ++d;
+    };
+    std::vector<size_t> members;
+    while (i > 0 && members.size() < (size_t)kAdjRun) {
+      const size_t k = i - 1;
+      if (plan->sigma[k] == 0) {
+        --i;
+        continue;
+      }
+      const uint64_t rr = reduce(plan->ox[k]);
+      if (rr != 0) {
+        if (d >= kAdjD) break;
+        add_vec(rr);
+      }
+      members.push_back(k);
+      --i;
+    }
+    if (members.empty()) continue;
+    uint64_t usedbits = 0;
+    for (int b = 0; b < d; ++b) usedbits |= 1ULL << piv[b];
+    for (int bit = phi->n - 1; bit >= 0 && d < kAdjD; --bit)
+      if (!((usedbits >> bit) & 1ULL)) {
+        add_vec(1ULL << bit);
+        usedbits |= 1ULL << bit;
+      }
+    AdjRunDev run;
+    std::memset(&run, 0, sizeof(run));
+    for (int e = 0; e < (1 << kAdjD); ++e) {
+      uint64_t so = 0;
+      for (int b = 0; b < kAdjD; ++b)
+        if ((e >> b) & 1) so ^= basis[b];
+      run.soff[e] = so;
+    }
+    for (int b = 0; b < kAdjD; ++b) run.piv[b] = piv[b];
+    run.count = (int32_t)members.size();
+    for (size_t j = 0; j < members.size(); ++j) {
+      const size_t k = members[j];
+      const uint64_t x = plan->ox[k], z = plan->oz[k];
+      const int s0 = anticommute(x, z, q0.x, q0.z) ? -1 : 1;
+      const double beta = s0 * plan->beta[k];
+      AdjRotDev &r = run.rot[j];
+      r.z = z;
+      r.c = std::cos(0.5 * beta);
+      r.s = std::sin(0.5 * beta);
+      r.u = 0;
+      for (int b = 0; b < kAdjD; ++b)
+        if ((x >> piv[b]) & 1ULL) r.u |= 1 << b;
+      r.ny = popc64(x & z) & 3;
+      r.zt = 0;
+      for (int e = 0; e < (1 << kAdjD); ++e) r.zt |= (uint32_t)(popc64(run.soff[e] & z) & 1) << e;
+      r.row = (int32_t)k;
+    }
+    const int tr = trace_begin(phi);
+    if (phi->dtype == SV_C128)
+      k_adjoint_run<double><<<blocks, kThreads, 0, phi->stream>>>((double2 *)phi->amps, (double2 *)lam->amps,
+                                                                  n_cosets, run, blocks, phi->d_partials);
+    else
+      k_adjoint_run<float><<<blocks, kThreads, 0, phi->stream>>>((float2 *)phi->amps, (float2 *)lam->amps,
+                                                                 n_cosets, run, blocks, phi->d_partials);
+    PR_CHECK_LAUNCH();
+    trace_end(phi, tr, KN_ADJOINT, 4.0 * (double)amp_bytes(phi->dtype) * (double)(1ULL << phi->n));
+  }
+  return SV_OK;
 }
 
 }  // namespace
@@ -157,9 +438,15 @@ int rotation_grads(sv_state *psi0, const uint64_t *x, const uint64_t *z, const d
   sv_plan *plan = nullptr;
   int rc = plan_create(&plan, psi0->n, psi0->dtype, x, z, angles, n_rot, -1, psi0->stream);
   if (rc) return rc;
-  sv_state *phi = nullptr, *lam = nullptr;
-  rc = sv_alloc(&phi, psi0->n, psi0->dtype, psi0->stream);
-  if (!rc) rc = sv_alloc(&lam, psi0->n, psi0->dtype, psi0->stream);
+  // phi and lambda live on psi0 between calls (allocated once per size and type)
+  for (sv_state *&w : psi0->work)
+    if (!rc && (!w || w->n != psi0->n || w->dtype != psi0->dtype)) {
+      sv_free(w);
+      w = nullptr;
+      rc = sv_alloc(&w, psi0->n, psi0->dtype, psi0->stream);
+    }
+  sv_state *phi = psi0->work[0], *lam = psi0->work[1];
+  if (!rc) phi->stream = lam->stream = psi0->stream;
   const Pauli q0 = psi0->frame;
   if (!rc) rc = sv_copy(phi, psi0);
   if (!rc) rc = apply_plan(phi, plan);
@@ -167,9 +454,13 @@ int rotation_grads(sv_state *psi0, const uint64_t *x, const uint64_t *z, const d
   if (!rc) rc = expval_impl(phi, hx, hz, hc, n_terms, &energy, nullptr);
   if (!rc) rc = pauli_sum_impl(lam, phi, hx, hz, hc, n_terms);
   const size_t L = plan ? plan->order.size() : 0;
-  const int blocks = step_blocks(psi0->n);
+  // fused backward runs (a coset of kAdjD dimensions per thread); states with
+  // fewer qubits take one pass per rotation
+  const bool fused = psi0->n >= kAdjD;
+  const int blocks = fused ? run_blocks(psi0) : step_blocks(psi0->n);
   if (!rc) rc = ensure_scratch(phi, (size_t)blocks * (L ? L : 1), L ? L : 1);
-  if (!rc) {
+  if (!rc && fused && L) rc = adjoint_runs(phi, lam, plan, q0, blocks);
+  if (!rc && !fused) {
     for (size_t i = L; i-- > 0;) {
       if (plan->sigma[i] == 0) {
         // identity string: only a global phase, zero gradient; keep a zero row
@@ -207,8 +498,6 @@ int rotation_grads(sv_state *psi0, const uint64_t *x, const uint64_t *z, const d
     }
     if (out_energy) *out_energy = energy;
   }
-  sv_free(lam);
-  sv_free(phi);
   plan_free(plan);
   return rc;
 }

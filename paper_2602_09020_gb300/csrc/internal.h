@@ -168,6 +168,9 @@ struct sv_state {
   size_t stage_cap = 0;
   void *h_stage = nullptr;
   size_t h_stage_cap = 0;
+  // work states of rotation_grads (phi and lambda), kept for the next call and
+  // released with this handle
+  sv_state *work[2] = {nullptr, nullptr};
   // tracing
   bool tracing = false;
   std::vector<cudaEvent_t> events;

@@ -273,6 +273,10 @@ int sv_free(sv_state *sv) {
   batch_forget(sv, nullptr);
   if (sv->stream) cudaStreamSynchronize(sv->stream);
   else cudaDeviceSynchronize();
+  for (sv_state *&w : sv->work) {
+    sv_free(w);
+    w = nullptr;
+  }
   if (sv->owns && sv->amps) cudaFree(sv->amps);
   if (sv->d_partials) cudaFree(sv->d_partials);
   if (sv->d_results) cudaFree(sv->d_results);
