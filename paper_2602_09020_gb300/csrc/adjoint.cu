@@ -117,16 +117,16 @@ __global__ void __launch_bounds__(kThreads)
 // x-masks span <= kAdjD dimensions is walked backwards coset by coset: a thread
 // keeps one coset of phi and of lambda in FP64 registers and, for each rotation
 // of the run (latest first), adds the coset's share of Im<lambda|P_j|phi> to a
-// per-rotation accumulator, then applies R_j^dag = c + i s P_j to both.  One
-// read and one write of phi and lambda per run instead of per rotation; the
-// arithmetic per rotation is that of k_adjoint_step.
+// per-rotation accumulator, then applies R_j^dag (tan form, below) to both.
+// One read and one write of phi and lambda per run instead of per rotation.
 
 constexpr int kAdjD = 3;     // run span dimension: 8 elements per coset
 constexpr int kAdjRun = 20;  // rotations per run (shared-memory accumulators)
 
 struct AdjRotDev {
   uint64_t z;
-  double c, s;   // R(-beta) = c + i s P
+  double t;      // R(-beta) = cos(beta/2) (1 + i t P), t = tan(beta/2)
+  double unused;
   int32_t u;     // coordinates of x in the run basis
   int32_t ny;    // popc(x & z) mod 4
   uint32_t zt;   // bit e = parity(soff[e] & z)
@@ -136,6 +136,7 @@ struct AdjRunDev {
   uint64_t soff[1 << kAdjD];
   int32_t piv[kAdjD];  // ascending
   int32_t count;
+  double scale;  // product of cos(beta/2) over the run: restores the stored states
   AdjRotDev rot[kAdjRun];  // backward order
 };
 
@@ -168,23 +169,25 @@ __device__ __forceinline__ double im_conj_ipow(double2 a, double2 b) {
 // One rotation on a coset, U = pairing pattern, K = nY mod 4.  With
 // (P v)_e = i^K (-1)^{sigma_m} v_m for the partner m = e ^ U:
 //   g   += (-1)^{sigma_m} Im(conj(lambda_e) i^K phi_m) + (e <-> m),
-//   v_e <- c v_e + s (-1)^{sigma_m} i^{K+1} v_m     (R^dag = c + i s P),
-// so the phase costs swaps and negations only.
+//   v_e <- v_e + t (-1)^{sigma_m} i^{K+1} v_m     (R^dag = cos (1 + i t P)),
+// so the phase costs swaps and negations only.  The factor cos(beta/2) is left
+// out: inside a run both vectors carry the same known scale, which the host
+// folds into each gradient and the kernel into the stored states.
 template <int U, int K>
 __device__ __forceinline__ void adj_rot(double2 (&p)[1 << kAdjD], double2 (&l)[1 << kAdjD], const AdjRotDev &r,
                                         int sig, double &g) {
   constexpr int E = 1 << kAdjD;
-  const double c = r.c, s = r.s;
+  const double t = r.t;
   if constexpr (U == 0) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const bool neg = (sig ^ (int)(r.zt >> e)) & 1;
-      const double ss = neg ? -s : s;
+      const double ts = neg ? -t : t;
       const double2 pe = p[e], le = l[e];
       const double ge = im_conj_mul(le, pe);
       g += neg ? -ge : ge;
-      p[e] = make_double2(c * pe.x - ss * pe.y, c * pe.y + ss * pe.x);
-      l[e] = make_double2(c * le.x - ss * le.y, c * le.y + ss * le.x);
+      p[e] = make_double2(pe.x - ts * pe.y, pe.y + ts * pe.x);
+      l[e] = make_double2(le.x - ts * le.y, le.y + ts * le.x);
     }
   } else {
     constexpr int H = adj_high_bit(U);
@@ -196,12 +199,12 @@ __device__ __forceinline__ void adj_rot(double2 (&p)[1 << kAdjD], double2 (&l)[1
       const double2 pe = p[e], pm = p[m], le = l[e], lm = l[m];
       const double ge = im_conj_ipow<K>(le, pm), gm = im_conj_ipow<K>(lm, pe);
       g += (nm ? -ge : ge) + (ne ? -gm : gm);
-      const double se = ne ? -s : s, sm = nm ? -s : s;
+      const double te = ne ? -t : t, tm = nm ? -t : t;
       const double2 wpm = ipow<K + 1>(pm), wpe = ipow<K + 1>(pe), wlm = ipow<K + 1>(lm), wle = ipow<K + 1>(le);
-      p[e] = make_double2(c * pe.x + sm * wpm.x, c * pe.y + sm * wpm.y);
-      p[m] = make_double2(c * pm.x + se * wpe.x, c * pm.y + se * wpe.y);
-      l[e] = make_double2(c * le.x + sm * wlm.x, c * le.y + sm * wlm.y);
-      l[m] = make_double2(c * lm.x + se * wle.x, c * lm.y + se * wle.y);
+      p[e] = make_double2(pe.x + tm * wpm.x, pe.y + tm * wpm.y);
+      p[m] = make_double2(pm.x + te * wpe.x, pm.y + te * wpe.y);
+      l[e] = make_double2(le.x + tm * wlm.x, le.y + tm * wlm.y);
+      l[m] = make_double2(lm.x + te * wle.x, lm.y + te * wle.y);
     }
   }
 }
@@ -255,14 +258,15 @@ __global__ void __launch_bounds__(kThreads)
       adj_dispatch(r.u * 4 + r.ny, p, l, r, sig, g);  // x = 0 has nY = 0
       sacc[j][threadIdx.x] += g;
     }
+    const double sc = run.scale;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       C o;
-      o.x = (R)p[e].x;
-      o.y = (R)p[e].y;
+      o.x = (R)(sc * p[e].x);
+      o.y = (R)(sc * p[e].y);
       phi[rep ^ run.soff[e]] = o;
-      o.x = (R)l[e].x;
-      o.y = (R)l[e].y;
+      o.x = (R)(sc * l[e].x);
+      o.y = (R)(sc * l[e].y);
       lam[rep ^ run.soff[e]] = o;
     }
   }
@@ -315,7 +319,8 @@ int run_blocks(const sv_state *sv) { return sv->dtype == SV_C128 ? run_blocks_t<
 // greedily into runs of <= kAdjRun whose x-masks span <= kAdjD dimensions.
 // Identity strings change only a global phase of both vectors (skipped); their
 // gradient rows stay zero.
-int adjoint_runs(sv_state *phi, sv_state *lam, const sv_plan *plan, const Pauli &q0, int blocks) {
+int adjoint_runs(sv_state *phi, sv_state *lam, const sv_plan *plan, const Pauli &q0, int blocks,
+                 std::vector<double> &gscale) {
   const size_t L = plan->order.size();
   PR_CUDA(cudaMemsetAsync(phi->d_partials, 0, sizeof(double) * (size_t)blocks * L, phi->stream));
   const uint64_t n_cosets = (1ULL << phi->n) >> kAdjD;
@@ -376,6 +381,7 @@ int adjoint_runs(sv_state *phi, sv_state *lam, const sv_plan *plan, const Pauli 
     }
     for (int b = 0; b < kAdjD; ++b) run.piv[b] = piv[b];
     run.count = (int32_t)members.size();
+    double cprod = 1.0;  // cos(beta/2) of the rotations of this run already undone
     for (size_t j = 0; j < members.size(); ++j) {
       const size_t k = members[j];
       const uint64_t x = plan->ox[k], z = plan->oz[k];
@@ -383,8 +389,9 @@ int adjoint_runs(sv_state *phi, sv_state *lam, const sv_plan *plan, const Pauli 
       const double beta = s0 * plan->beta[k];
       AdjRotDev &r = run.rot[j];
       r.z = z;
-      r.c = std::cos(0.5 * beta);
-      r.s = std::sin(0.5 * beta);
+      r.t = std::tan(0.5 * beta);
+      gscale[k] = cprod * cprod;  // both vectors carry 1/cprod at this rotation
+      cprod *= std::cos(0.5 * beta);
       r.u = 0;
       for (int b = 0; b < kAdjD; ++b)
         if ((x >> piv[b]) & 1ULL) r.u |= 1 << b;
@@ -393,6 +400,7 @@ int adjoint_runs(sv_state *phi, sv_state *lam, const sv_plan *plan, const Pauli 
       for (int e = 0; e < (1 << kAdjD); ++e) r.zt |= (uint32_t)(popc64(run.soff[e] & z) & 1) << e;
       r.row = (int32_t)k;
     }
+    run.scale = cprod;
     const int tr = trace_begin(phi);
     if (phi->dtype == SV_C128)
       k_adjoint_run<double><<<blocks, kThreads, 0, phi->stream>>>((double2 *)phi->amps, (double2 *)lam->amps,
@@ -459,7 +467,8 @@ int rotation_grads(sv_state *psi0, const uint64_t *x, const uint64_t *z, const d
   const bool fused = psi0->n >= kAdjD;
   const int blocks = fused ? run_blocks(psi0) : step_blocks(psi0->n);
   if (!rc) rc = ensure_scratch(phi, (size_t)blocks * (L ? L : 1), L ? L : 1);
-  if (!rc && fused && L) rc = adjoint_runs(phi, lam, plan, q0, blocks);
+  std::vector<double> gscale(L, 1.0);
+  if (!rc && fused && L) rc = adjoint_runs(phi, lam, plan, q0, blocks, gscale);
   if (!rc && !fused) {
     for (size_t i = L; i-- > 0;) {
       if (plan->sigma[i] == 0) {
@@ -494,7 +503,7 @@ int rotation_grads(sv_state *psi0, const uint64_t *x, const uint64_t *z, const d
     for (size_t i = 0; i < L; ++i) {
       if (plan->sigma[i] == 0) continue;
       const int s0 = anticommute(plan->ox[i], plan->oz[i], q0.x, q0.z) ? -1 : 1;
-      out_grads[plan->order[i]] = (double)(s0 * plan->sigma[i]) * phi->h_results[i];
+      out_grads[plan->order[i]] = (double)(s0 * plan->sigma[i]) * gscale[i] * phi->h_results[i];
     }
     if (out_energy) *out_energy = energy;
   }
