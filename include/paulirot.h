@@ -16,6 +16,14 @@
  *   * First-order Trotter products, Eq. (trotter), and a symmetric
  *     second-order product (not in the paper; see trotter_expand).
  *   * dE/dtheta_j of E = <psi|H|psi> by an adjoint sweep (not in the paper).
+ *   * General Clifford frames in the backward interpretation (Sec.
+ *     "Clifford-Fullstate Hybrid Simulator"): Clifford gates update a host
+ *     frame, non-Clifford rotations run on the state about the rewritten
+ *     axis, the frame is applied to the state as <= 4n rotations by pi/2
+ *     (App. "Efficiently implementing Clifford unitaries with multi-qubit
+ *     rotations"), and Pauli measurement / qubit preparation act on the
+ *     rewritten axis (App. "Complete workflow of the hybrid Clifford
+ *     fullstate simulation"); see the cliff_* and cfhs_* calls.
  *
  * Conventions
  *   * qubit j is bit j of the amplitude index (qubit 0 least significant);
