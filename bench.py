@@ -261,6 +261,7 @@ def run_ours(a):
         plan = capi.plan_create(a.n, dtype, rx, rz, rt, a.fusion_depth, sh)
         plan_ms = 1000.0 * (time.perf_counter() - t0)
         nrot, nruns, ndiag = capi.plan_stats(plan)
+        dmax = a.fusion_depth if a.fusion_depth >= 0 else capi.plan_tuned_depth(a.n, dtype)[0]
         sv = capi.sv_alloc(a.n, dtype, sh)
         out = {}
 
@@ -288,7 +289,7 @@ def run_ours(a):
         ms = [e0.elapsed_time(e1) for e0, e1 in ev]
         capi.sv_free(sv)
         capi.plan_free(plan)
-        return {"ms": ms, "plan_ms": plan_ms, "runs": nruns, "diag_runs": ndiag, "nrot": nrot,
+        return {"ms": ms, "plan_ms": plan_ms, "runs": nruns, "dmax": dmax, "diag_runs": ndiag, "nrot": nrot,
                 "trace": rows, "clocks": ck, "energy": out["energy"], "norm2": out["norm2"]}
 
     def roofline(rows: dict, steps: int, dtype: str):
@@ -317,6 +318,19 @@ def run_ours(a):
         roof.update(common)
         return roof, sum(r[0] for r in rows.values())
 
+    # the fusion depth plan_create(-1) takes comes from the library's autotuner,
+    # run on the step's own rotation list for each precision (untimed setup)
+    tuning = {}
+    if a.fusion_depth < 0:
+        for dt_name in ([a.dtype] if a.skip_extras else [a.dtype, "c128" if a.dtype == "c64" else "c64"]):
+            svt = capi.sv_alloc(a.n, dt_name, sh)
+            t0 = time.perf_counter()
+            depth, tms = capi.plan_autotune(svt, rx, rz, rt, reps=1)
+            tuning[dt_name] = {"depth": depth, "tune_s": time.perf_counter() - t0,
+                               "ms_per_list_by_depth": {str(d + 1): v for d, v in enumerate(tms) if v > 0}}
+            capi.sv_free(svt)
+        barrier()
+
     clocks = Clocks(dev)
     # the headline steps run untraced: per-launch event records between the
     # kernels would keep consecutive passes from overlapping (programmatic
@@ -339,7 +353,7 @@ def run_ours(a):
         o = measure(other, max(1, min(a.steps, 2)), 1, True)
         o_roof, _ = roofline(o["trace"], max(1, min(a.steps, 2)), other)
         extras[other] = {"value": R / (statistics.mean(o["ms"]) / 1000.0), "ms_per_step": statistics.mean(o["ms"]),
-                         "passes_per_step": o["runs"], "energy": o["energy"], "roofline": o_roof}
+                         "passes_per_step": o["runs"], "fusion_depth": o["dmax"], "energy": o["energy"], "roofline": o_roof}
         # gate-decomposed path on the same GPU, same dtype: a strided sample of one Trotter step
         sample = slice(0, a.terms, 4)
         gx, gz, gt = rx[sample], rz[sample], rt[sample]
@@ -423,7 +437,8 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": "rotations/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": a.dtype, "data": "synthetic (seeded JW-shaped Hamiltonian)",
-        "config": config_dict(a, a.dtype),
+        "config": dict(config_dict(a, a.dtype), fusion_depth=main["dmax"],
+                       fusion_depth_source="autotuned" if a.fusion_depth < 0 else "--fusion-depth"),
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -434,6 +449,7 @@ def run_ours(a):
         "effective_gbs": R * sweep_bytes / (ms_step / 1000.0) / 1e9,
         "rescaled_runtime_s": (ms_step / 1000.0) / (R * (1 << a.n)),
         "plan_ms": main["plan_ms"], "energy": main["energy"], "norm2": main["norm2"],
+        "fusion_depth_tuning": tuning or None,
         "kernels": {k: {"launches": v[0], "ms": v[1], "gbs": (v[2] / (v[1] / 1000.0) / 1e9) if v[1] else None,
                         "tflops": (v[3] / (v[1] / 1000.0) / 1e12) if v[1] else None}
                     for k, v in traced["trace"].items()},

@@ -147,7 +147,8 @@ int apply_pauli_rotations(sv_state *sv, const uint64_t *x, const uint64_t *z,
 
 /* Compile a rotation list once for states of n qubits and this dtype.
  * fusion_depth = maximum dimension of the span of x-masks fused into one
- * pass (0..5; -1 = tuned default for the dtype).  The plan's device buffers
+ * pass (0..5; -1 = the depth plan_tuned_depth reports: the autotuned one for
+ * (n, dtype) if one is recorded, else 3 for complex128 and 4 for complex64).  The plan's device buffers
  * are uploaded on cuda_stream; plan_apply then launches kernels only (no
  * host-to-device copy), so it can be captured into a CUDA graph. */
 int plan_create(sv_plan **out, int n_qubits, int dtype, const uint64_t *x, const uint64_t *z,
@@ -159,6 +160,42 @@ int plan_create(sv_plan **out, int n_qubits, int dtype, const uint64_t *x, const
 int plan_apply(sv_state *sv, sv_plan *plan);
 
 int plan_free(sv_plan *plan);
+
+/* ---- fusion-depth autotuner ----------------------------------------------------
+ * The best fusion depth trades HBM passes against per-pass work and depends on
+ * the kernel variant, n and the rotation list (fused pass of the paper's
+ * Sec. "Implementation"; the depth is not fixed there).  A process-wide table
+ * maps (n, dtype) to a depth that plan_create(-1) and apply_pauli_rotations
+ * use.  If the environment variable PAULIROT_TUNE_CACHE names a file, the table
+ * is read from it before its first use and written back after each
+ * plan_autotune; the file holds "<c64|c128> <n> <depth>" lines.
+ *
+ * plan_autotune compiles x/z/angles (count rotations, as for plan_create) at
+ * every depth 1..max_depth (max_depth <= 0 means 5; capped at n), applies each
+ * plan once untimed and then reps times (reps <= 0 means 3) in two interleaved
+ * rounds on sv's stream, timed with CUDA events, and records the fastest
+ * depth for (sv's n, sv's dtype); ties go to the smaller depth.  sv is the
+ * scratch: its represented state is overwritten (evolved by the timed
+ * applications), so initialise it afterwards.  out_ms (nullable, 5 doubles)
+ * receives the milliseconds per application for depths 1..5, -1 where not
+ * timed.  Batched launches take plans of depth <= 4: tune with max_depth 4
+ * for them.  Synchronizes sv's stream. */
+int plan_autotune(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *angles, size_t count,
+                  int max_depth, int reps, int *out_depth, double *out_ms);
+
+/* The depth plan_create(-1) would use for (n, dtype) (capped at n);
+ * *out_tuned (nullable) = 1 if it comes from the table, 0 if it is the default. */
+int plan_tuned_depth(int n_qubits, int dtype, int *out_depth, int *out_tuned);
+
+/* Record depth (1..5) for (n, dtype) in the table, or remove the entry
+ * (depth = -1).  Host only; does not write the cache file. */
+int plan_set_tuned_depth(int n_qubits, int dtype, int depth);
+
+/* Merge the entries of a cache file into the table (a missing file is empty;
+ * a malformed one is SV_EINVAL and changes nothing), or write the table to a
+ * file (through a temporary file renamed over it).  Host only. */
+int plan_tune_cache_load(const char *path);
+int plan_tune_cache_save(const char *path);
 
 /* Plan statistics: number of rotations (after dropping identities), number
  * of fused runs (= HBM passes), of which diagonal phase-sum runs. */

@@ -79,6 +79,11 @@ def lib() -> ctypes.CDLL:
         "plan_apply": ([vp, vp], i),
         "plan_free": ([vp], i),
         "plan_stats": ([vp, P(sz), P(sz), P(sz)], i),
+        "plan_autotune": ([vp, vp, vp, vp, sz, i, i, P(i), vp], i),
+        "plan_tuned_depth": ([i, i, P(i), P(i)], i),
+        "plan_set_tuned_depth": ([i, i, i], i),
+        "plan_tune_cache_load": ([ctypes.c_char_p], i),
+        "plan_tune_cache_save": ([ctypes.c_char_p], i),
         "trotter_expand": ([vp, vp, vp, sz, d, i, i, i, vp, vp, vp, sz, P(sz)], i),
         "expval_pauli_sum": ([vp, vp, vp, vp, sz, P(d), P(d)], i),
         "expval_pauli_sum_noalloc": ([vp, vp, vp, vp, sz, P(d), P(d)], i),
@@ -119,6 +124,8 @@ def exported_symbols() -> Sequence[str]:
             "sv_device_ptr", "sv_info", "sv_set_basis_state", "sv_from_host", "sv_to_host",
             "sv_materialize", "sv_copy", "frame_reset", "frame_apply_pauli", "frame_get",
             "apply_pauli_rotations", "plan_create", "plan_apply", "plan_free", "plan_stats",
+            "plan_autotune", "plan_tuned_depth", "plan_set_tuned_depth", "plan_tune_cache_load",
+            "plan_tune_cache_save",
             "trotter_expand", "expval_pauli_sum", "expval_pauli_sum_noalloc", "apply_pauli_sum", "rotation_grads",
             "apply_pauli_rotations_gates", "batch_run", "batch_run_ex", "batch_info", "sv_trace_start",
             "sv_trace_stop", "cliff_create", "cliff_free", "cliff_reset", "cliff_num_qubits", "cliff_apply_gates",
@@ -259,6 +266,38 @@ def plan_stats(plan: int) -> Tuple[int, int, int]:
     a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
     _check(lib().plan_stats(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def plan_autotune(sv: int, x, z, angles, max_depth: int = 0, reps: int = 0) -> Tuple[int, np.ndarray]:
+    """Time the list at every fusion depth on sv (overwritten) and record the
+    fastest for sv's (n, dtype).  Returns (depth, ms per application for
+    depths 1..5, -1 where not timed)."""
+    x, z, a = _u64(x), _u64(z), _f64(angles)
+    if not (len(x) == len(z) == len(a)):
+        raise ValueError("x, z and angles must have equal length")
+    d = ctypes.c_int()
+    ms = np.empty(5, np.float64)
+    _check(lib().plan_autotune(sv, _p(x), _p(z), _p(a), len(a), int(max_depth), int(reps), ctypes.byref(d),
+                               _p(ms)))
+    return d.value, ms
+
+
+def plan_tuned_depth(n_qubits: int, dtype) -> Tuple[int, bool]:
+    d, t = ctypes.c_int(), ctypes.c_int()
+    _check(lib().plan_tuned_depth(int(n_qubits), dtype_code(dtype), ctypes.byref(d), ctypes.byref(t)))
+    return d.value, bool(t.value)
+
+
+def plan_set_tuned_depth(n_qubits: int, dtype, depth: int) -> None:
+    _check(lib().plan_set_tuned_depth(int(n_qubits), dtype_code(dtype), int(depth)))
+
+
+def plan_tune_cache_load(path: str) -> None:
+    _check(lib().plan_tune_cache_load(os.fsencode(path)))
+
+
+def plan_tune_cache_save(path: str) -> None:
+    _check(lib().plan_tune_cache_save(os.fsencode(path)))
 
 
 def trotter_expand(x, z, c, dt: float, steps: int, order: int = 1, merge: bool = False):

@@ -22,6 +22,8 @@ constexpr int kThreads = 256;
 
 inline int max_qubits(int dtype) { return dtype == SV_C128 ? 33 : 34; }
 inline size_t amp_bytes(int dtype) { return dtype == SV_C128 ? 16 : 8; }
+// fusion depth of plan_create(-1) when no tuned value is recorded
+inline int default_depth(int dtype) { return dtype == SV_C128 ? 3 : 4; }
 
 // ---------------------------------------------------------------- errors
 int fail(int code, const char *fmt, ...);
@@ -223,6 +225,8 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
                const double *theta, size_t count, int fusion_depth, cudaStream_t stream);
 int apply_plan(sv_state *sv, sv_plan *plan);
 int validate_masks(int n, const uint64_t *x, const uint64_t *z, size_t count);
+// tuned fusion depth for (n, dtype), or -1 if none is recorded (tune.cu)
+int tuned_depth(int n, int dtype);
 
 // reductions (reduce.cu)
 int expval_impl(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c, size_t count,

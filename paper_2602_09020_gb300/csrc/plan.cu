@@ -31,8 +31,6 @@ struct Item {
 // fold thresholds on log2 of the amplitude growth bound since the last fold
 double fold_half(int dtype) { return dtype == SV_C128 ? 400.0 : 30.0; }
 
-int default_depth(int dtype) { return dtype == SV_C128 ? 3 : 4; }
-
 uint64_t fixed_half_angle(double theta) {
   // theta/2 as a fraction of a full turn in units of 2^-64 (wraps mod 2 pi)
   double q = theta / (4.0 * kPi);
@@ -94,7 +92,11 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
   if (rc) return rc;
   for (size_t j = 0; j < count; ++j)
     if (!std::isfinite(theta[j])) return fail(SV_EINVAL, "angle %zu is not finite", j);
-  int dmax = fusion_depth < 0 ? default_depth(dtype) : fusion_depth;
+  int dmax = fusion_depth;
+  if (dmax < 0) {
+    const int t = tuned_depth(n, dtype);
+    dmax = t > 0 ? t : default_depth(dtype);
+  }
   if (dmax > kDMax) return fail(SV_EINVAL, "fusion_depth must be <= %d", kDMax);
   if (dmax > n) dmax = n;
 
