@@ -319,15 +319,16 @@ def run_ours(a):
         return roof, sum(r[0] for r in rows.values())
 
     # the fusion depth plan_create(-1) takes comes from the library's autotuner,
-    # run on the step's own rotation list for each precision (untimed setup)
+    # run on the first Trotter step of the list for each precision (untimed setup)
     tuning = {}
     if a.fusion_depth < 0:
         for dt_name in ([a.dtype] if a.skip_extras else [a.dtype, "c128" if a.dtype == "c64" else "c64"]):
             svt = capi.sv_alloc(a.n, dt_name, sh)
             t0 = time.perf_counter()
-            depth, tms = capi.plan_autotune(svt, rx, rz, rt, reps=1)
+            depth, tms = capi.plan_autotune(svt, rx[:a.terms], rz[:a.terms], rt[:a.terms], reps=2)
             tuning[dt_name] = {"depth": depth, "tune_s": time.perf_counter() - t0,
-                               "ms_per_list_by_depth": {str(d + 1): v for d, v in enumerate(tms) if v > 0}}
+                               "sample": f"first {a.terms} rotations",
+                               "ms_per_sample_by_depth": {str(d + 1): v for d, v in enumerate(tms) if v > 0}}
             capi.sv_free(svt)
         barrier()
 
