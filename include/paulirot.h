@@ -324,6 +324,16 @@ typedef struct sv_trace_row {
  * (on the handle's stream).  Recording adds two event records per launch. */
 int sv_trace_start(sv_state *sv);
 
+/* Trace modes.  SV_TRACE_LAUNCHES = sv_trace_start.  SV_TRACE_BLOCKS records one
+ * event wherever the launched kernel changes (and one at sv_trace_stop): a
+ * block of consecutive launches of one kernel runs as it does untraced
+ * (chained passes overlap their prologues), and its elapsed time, which
+ * includes anything else the handle enqueues inside the block, is
+ * attributed to that kernel.  SV_EINVAL for another mode. */
+#define SV_TRACE_LAUNCHES 0
+#define SV_TRACE_BLOCKS 1
+int sv_trace_start_ex(sv_state *sv, int mode);
+
 /* Stop recording, synchronise the stream and aggregate per kernel name into
  * rows (at most cap; *n_rows = rows written).  Events are recycled. */
 int sv_trace_stop(sv_state *sv, sv_trace_row *rows, int cap, int *n_rows);

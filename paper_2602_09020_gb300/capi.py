@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
         "batch_run_ex": ([vp, vp, sz, i, vp], i),
         "batch_info": ([P(i), P(i), P(i)], i),
         "sv_trace_start": ([vp], i),
+        "sv_trace_start_ex": ([vp, i], i),
         "sv_trace_stop": ([vp, vp, i, P(i)], i),
         "cliff_create": ([P(vp), i], i),
         "cliff_free": ([vp], i),
@@ -128,7 +129,7 @@ def exported_symbols() -> Sequence[str]:
             "plan_tune_cache_save",
             "trotter_expand", "expval_pauli_sum", "expval_pauli_sum_noalloc", "apply_pauli_sum", "rotation_grads",
             "apply_pauli_rotations_gates", "batch_run", "batch_run_ex", "batch_info", "sv_trace_start",
-            "sv_trace_stop", "cliff_create", "cliff_free", "cliff_reset", "cliff_num_qubits", "cliff_apply_gates",
+            "sv_trace_start_ex", "sv_trace_stop", "cliff_create", "cliff_free", "cliff_reset", "cliff_num_qubits", "cliff_apply_gates",
             "cliff_map_paulis", "cliff_entry", "cliff_is_origin", "cliff_inverse_rotations", "cfhs_apply_gates",
             "cfhs_apply_rotations", "cfhs_expval", "cfhs_materialize", "cfhs_measure_pauli", "cfhs_prepare_qubit"]
 
@@ -384,8 +385,13 @@ class TraceRow(ctypes.Structure):
                 ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
-def sv_trace_start(sv: int) -> None:
-    _check(lib().sv_trace_start(sv))
+SV_TRACE_LAUNCHES, SV_TRACE_BLOCKS = 0, 1
+
+
+def sv_trace_start(sv: int, blocks: bool = False) -> None:
+    """Trace every launch (event pair each), or with blocks=True one event per
+    change of kernel (consecutive launches of one kernel stay chained)."""
+    _check(lib().sv_trace_start_ex(sv, SV_TRACE_BLOCKS if blocks else SV_TRACE_LAUNCHES))
 
 
 def sv_trace_stop(sv: int) -> dict:

@@ -401,7 +401,7 @@ int adjoint_runs(sv_state *phi, sv_state *lam, const sv_plan *plan, const Pauli 
       r.row = (int32_t)k;
     }
     run.scale = cprod;
-    const int tr = trace_begin(phi);
+    const int tr = trace_begin(phi, KN_ADJOINT);
     if (phi->dtype == SV_C128)
       k_adjoint_run<double><<<blocks, kThreads, 0, phi->stream>>>((double2 *)phi->amps, (double2 *)lam->amps,
                                                                   n_cosets, run, blocks, phi->d_partials);
@@ -420,7 +420,7 @@ int adjoint_step(sv_state *phi, sv_state *lam, uint64_t x, uint64_t z, double be
   const int blocks = step_blocks(phi->n);
   const double c = std::cos(0.5 * beta), s = std::sin(0.5 * beta);
   const uint64_t n_amps = 1ULL << phi->n;
-  const int tr = trace_begin(phi);
+  const int tr = trace_begin(phi, KN_ADJOINT);
   if (phi->dtype == SV_C128)
     k_adjoint_step<double><<<blocks, kThreads, 0, phi->stream>>>((double2 *)phi->amps, (double2 *)lam->amps,
                                                                  n_amps, x, z, c, s, d_out);

@@ -90,7 +90,7 @@ struct GateCtx {
 
 int hadamard(GateCtx &g, int q) {
   const uint64_t half = (1ULL << g.sv->n) >> 1;
-  const int tr = trace_begin(g.sv);
+  const int tr = trace_begin(g.sv, KN_GATE1);
   if (g.sv->dtype == SV_C128)
     k_hadamard<double><<<g.blocks_half, kThreads, 0, g.sv->stream>>>((double2 *)g.sv->amps, half, q);
   else
@@ -103,7 +103,7 @@ int hadamard(GateCtx &g, int q) {
 
 int diag1(GateCtx &g, int q, double2 p0, double2 p1) {
   const uint64_t half = (1ULL << g.sv->n) >> 1;
-  const int tr = trace_begin(g.sv);
+  const int tr = trace_begin(g.sv, KN_DIAG1);
   if (g.sv->dtype == SV_C128)
     k_diag1<double><<<g.blocks_half, kThreads, 0, g.sv->stream>>>((double2 *)g.sv->amps, half, q, p0, p1);
   else
@@ -117,7 +117,7 @@ int diag1(GateCtx &g, int q, double2 p0, double2 p1) {
 int cnot(GateCtx &g, int c, int t) {
   const uint64_t quarter = (1ULL << g.sv->n) >> 2;
   const int lo = c < t ? c : t, hi = c < t ? t : c;
-  const int tr = trace_begin(g.sv);
+  const int tr = trace_begin(g.sv, KN_CNOT);
   if (g.sv->dtype == SV_C128)
     k_cnot<double><<<g.blocks_quarter, kThreads, 0, g.sv->stream>>>((double2 *)g.sv->amps, quarter, lo, hi,
                                                                     1ULL << c, 1ULL << t);

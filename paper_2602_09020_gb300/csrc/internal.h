@@ -141,6 +141,7 @@ struct TraceRec {
   double bytes;   // algorithmic bytes of this launch
   double flops;   // algorithmic floating-point operations of this launch
   int ev0, ev1;   // event pool slots
+  int64_t launches;  // launches in the record (block mode: a run of one kernel)
 };
 // kernel name ids for tracing
 enum KernelId {
@@ -175,6 +176,7 @@ struct sv_state {
   sv_state *work[2] = {nullptr, nullptr};
   // tracing
   bool tracing = false;
+  bool trace_blocks = false;  // one event per change of kernel instead of per launch
   std::vector<cudaEvent_t> events;
   int events_used = 0;
   std::vector<pr::TraceRec> trace;
@@ -199,7 +201,7 @@ struct sv_plan {
 
 namespace pr {
 // tracing (trace.cu): call trace_begin before a launch and trace_end after it
-int trace_begin(sv_state *sv);
+int trace_begin(sv_state *sv, int name);
 void trace_end(sv_state *sv, int slot, int name, double bytes, double flops = 0.0);
 void trace_release(sv_state *sv);
 

@@ -80,7 +80,7 @@ int launch_project(sv_state *sv, const Pauli &M, double s, double scale) {
   const uint64_t count = M.x ? N / 2 : N;
   const uint64_t need = (count + kThreads - 1) / kThreads;
   const unsigned blocks = (unsigned)(need < (uint64_t)device_sm_count() * 8 ? (need ? need : 1) : device_sm_count() * 8);
-  const int tr = trace_begin(sv);
+  const int tr = trace_begin(sv, KN_PROJECT);
   k_project<R><<<blocks, kThreads, 0, sv->stream>>>((typename Cplx<R>::T *)sv->amps, count, M.x, M.z, h,
                                                     popc64(M.x & M.z) & 3, (R)s, (R)scale);
   PR_CHECK_LAUNCH();

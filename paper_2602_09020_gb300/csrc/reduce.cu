@@ -470,13 +470,13 @@ int run_expval_t(sv_state *sv, const std::vector<HostExpRun> &runs, const std::v
   int rc = ensure_scratch(sv, (size_t)2 * blocks * runs.size(), 2 * runs.size());
   if (rc) return rc;
   for (size_t r = 0; r < runs.size(); ++r) {
-    const int tr = trace_begin(sv);
+    const int tr = trace_begin(sv, KN_EXPVAL);
     k_expval<R, Idx, D><<<blocks, kThreads, 0, sv->stream>>>((const C *)sv->amps, (Idx)n_cosets, runs[r].dev,
                                                             dg[r], dt[r], sv->d_partials + 2 * blocks * r);
     PR_CHECK_LAUNCH();
     trace_end(sv, tr, KN_EXPVAL, (double)sizeof(C) * (double)(1ULL << sv->n));
   }
-  const int tr = trace_begin(sv);
+  const int tr = trace_begin(sv, KN_FINISH);
   k_finish<<<(unsigned)runs.size(), kThreads, 0, sv->stream>>>(sv->d_partials, blocks, sv->d_results);
   PR_CHECK_LAUNCH();
   trace_end(sv, tr, KN_FINISH, 16.0 * blocks * runs.size());
@@ -1057,7 +1057,7 @@ int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *ener
   // choose S from an estimate of <a|a>
   double *d_est = sv->d_results + kWTerms * runs.size();
   {
-    const int tr = trace_begin(sv);
+    const int tr = trace_begin(sv, KN_EXPVAL);
     k_norm_est<<<est_blocks, kThreads, 0, sv->stream>>>((const float2 *)sv->amps, n_amps, d_est);
     PR_CHECK_LAUNCH();
     trace_end(sv, tr, KN_EXPVAL, 8.0 * (double)n_amps);
@@ -1085,7 +1085,7 @@ int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *ener
   long long *res = (long long *)sv->d_results;
   for (size_t r = 0; r < runs.size(); ++r) {
     const char *base = (const char *)sv->d_stage + off[r];
-    const int tr = trace_begin(sv);
+    const int tr = trace_begin(sv, KN_EXPVAL);
     k_expval_fix<Idx><<<blocks, kWThreads, 0, sv->stream>>>(
         (const float2 *)sv->amps, (Idx)n_tiles, runs[r].dev, (const WhtGroupDev *)base,
         (const WhtTermDev *)(base + kGroupBytes), 14 - S, part + (size_t)kWTerms * blocks * r);
@@ -1093,7 +1093,7 @@ int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *ener
     trace_end(sv, tr, KN_EXPVAL, 8.0 * (double)n_amps);
   }
   {
-    const int tr = trace_begin(sv);
+    const int tr = trace_begin(sv, KN_FINISH);
     k_finish_fix<<<(unsigned)runs.size(), kThreads, 0, sv->stream>>>(part, blocks, res);
     PR_CHECK_LAUNCH();
     trace_end(sv, tr, KN_FINISH, 8.0 * kWTerms * blocks * runs.size());
@@ -1155,7 +1155,7 @@ static int run_pauli_sum_t(sv_state *dst, sv_state *src, const std::vector<HostE
   if (blocks < 1) blocks = 1;
   PR_CUDA(cudaMemsetAsync(dst->amps, 0, amp_bytes(dst->dtype) << dst->n, src->stream));
   for (size_t r = 0; r < runs.size(); ++r) {
-    const int tr = trace_begin(src);
+    const int tr = trace_begin(src, KN_PAULI_SUM);
     k_pauli_sum<R, Idx, D><<<blocks, kThreads, 0, src->stream>>>((C *)dst->amps, (const C *)src->amps,
                                                                     (Idx)n_cosets, runs[r].dev, dg[r], dt[r]);
     PR_CHECK_LAUNCH();

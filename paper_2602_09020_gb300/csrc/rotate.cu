@@ -75,7 +75,7 @@ int launch_coset_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_
   uint64_t need = (n_cosets + (uint64_t)kThreads * V - 1) / ((uint64_t)kThreads * V);
   unsigned blocks = (unsigned)(need < (uint64_t)cap ? need : (uint64_t)cap);
   if (!blocks) blocks = 1;
-  const int tr = trace_begin(sv);
+  const int tr = trace_begin(sv, KN_COSET0 + D);
   k_coset<R, Idx, D, V><<<blocks, kThreads, 0, sv->stream>>>((C *)sv->amps, (Idx)n_cosets, run,
                                                              plan->d_rots, fx, fz);
   PR_CHECK_LAUNCH();
@@ -101,7 +101,7 @@ int launch_c64x2_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_
   uint64_t need = (n_pairs + kThreads - 1) / kThreads;
   unsigned blocks = (unsigned)(need < (uint64_t)cap ? need : (uint64_t)cap);
   if (!blocks) blocks = 1;
-  const int tr = trace_begin(sv);
+  const int tr = trace_begin(sv, KN_COSET0 + D);
   // programmatic dependent launch: the grid never exceeds what the GPU holds at
   // once, so the early-scheduled CTAs of this pass cannot keep the previous
   // pass's CTAs from running, and each waits for that pass before touching
@@ -205,7 +205,7 @@ int launch_diag_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t
   uint64_t need = (n_groups + kThreads - 1) / kThreads;
   unsigned blocks = (unsigned)(need < (uint64_t)cap ? need : (uint64_t)cap);
   if (!blocks) blocks = 1;
-  const int tr = trace_begin(sv);
+  const int tr = trace_begin(sv, KN_DIAG_SUM);
   k_diag_sum<R, Idx><<<blocks, kThreads, 0, sv->stream>>>((C *)sv->amps, (Idx)n_groups, run, plan->d_diag,
                                                           fx, (const C *)tab);
   PR_CHECK_LAUNCH();

@@ -158,7 +158,7 @@ static unsigned grid_for(uint64_t work) {
 int launch_set_basis(sv_state *sv, uint64_t k) {
   size_t bytes = amp_bytes(sv->dtype) << sv->n;
   PR_CUDA(cudaMemsetAsync(sv->amps, 0, bytes, sv->stream));
-  const int tr = trace_begin(sv);
+  const int tr = trace_begin(sv, KN_SET_BASIS);
   if (sv->dtype == SV_C128)
     k_set_one<double2><<<1, 1, 0, sv->stream>>>((double2 *)sv->amps, k);
   else
@@ -171,7 +171,7 @@ int launch_set_basis(sv_state *sv, uint64_t k) {
 int launch_materialize(sv_state *sv, uint64_t x, uint64_t z, int q) {
   uint64_t n_amps = 1ULL << sv->n;
   unsigned g = grid_for(x ? n_amps / 2 : n_amps);
-  const int tr = trace_begin(sv);
+  const int tr = trace_begin(sv, KN_MATERIALIZE);
   if (sv->dtype == SV_C128)
     k_materialize<double, double2><<<g, kThreads, 0, sv->stream>>>((double2 *)sv->amps, n_amps, x, z, q);
   else
@@ -184,7 +184,7 @@ int launch_materialize(sv_state *sv, uint64_t x, uint64_t z, int q) {
 int launch_scale(sv_state *sv, double re, double im) {
   uint64_t n_amps = 1ULL << sv->n;
   unsigned g = grid_for(n_amps);
-  const int tr = trace_begin(sv);
+  const int tr = trace_begin(sv, KN_SCALE);
   if (sv->dtype == SV_C128)
     k_scale<double, double2><<<g, kThreads, 0, sv->stream>>>((double2 *)sv->amps, n_amps, re, im);
   else

@@ -1,4 +1,7 @@
-// Per-launch CUDA-event tracing for a state handle.
+// CUDA-event tracing for a state handle: an event pair around every launch, or
+// (block mode) one event wherever the kernel changes, so consecutive launches of
+// one kernel keep running back to back (chained passes overlap) and their
+// average time is the block's time over its launches.
 #include <cstring>
 
 #include "internal.h"
@@ -22,8 +25,18 @@ static int next_event(sv_state *sv) {
   return sv->events_used++;
 }
 
-int trace_begin(sv_state *sv) {
+int trace_begin(sv_state *sv, int name) {
   if (!sv || !sv->tracing) return -1;
+  if (sv->trace_blocks) {
+    // one event where the kernel changes: it ends the open block and opens the next
+    if (!sv->trace.empty() && sv->trace.back().name == name) return (int)sv->trace.size() - 1;
+    int e = next_event(sv);
+    if (e < 0) return -1;
+    cudaEventRecord(sv->events[e], sv->stream);
+    if (!sv->trace.empty()) sv->trace.back().ev1 = e;
+    sv->trace.push_back(TraceRec{name, 0.0, 0.0, e, -1, 0});
+    return (int)sv->trace.size() - 1;
+  }
   int s = next_event(sv);
   if (s < 0) return -1;
   cudaEventRecord(sv->events[s], sv->stream);
@@ -32,10 +45,17 @@ int trace_begin(sv_state *sv) {
 
 void trace_end(sv_state *sv, int slot, int name, double bytes, double flops) {
   if (!sv || !sv->tracing || slot < 0) return;
+  if (sv->trace_blocks) {
+    TraceRec &r = sv->trace[slot];
+    r.bytes += bytes;
+    r.flops += flops;
+    r.launches += 1;
+    return;
+  }
   int e = next_event(sv);
   if (e < 0) return;
   cudaEventRecord(sv->events[e], sv->stream);
-  sv->trace.push_back(TraceRec{name, bytes, flops, slot, e});
+  sv->trace.push_back(TraceRec{name, bytes, flops, slot, e, 1});
 }
 
 void trace_release(sv_state *sv) {
@@ -51,17 +71,32 @@ using namespace pr;
 
 extern "C" {
 
-int sv_trace_start(sv_state *sv) {
+int sv_trace_start_ex(sv_state *sv, int mode) {
   if (!sv) return fail(SV_EINVAL, "sv is NULL");
+  if (mode != SV_TRACE_LAUNCHES && mode != SV_TRACE_BLOCKS) return fail(SV_EINVAL, "bad trace mode %d", mode);
   sv->tracing = true;
+  sv->trace_blocks = mode == SV_TRACE_BLOCKS;
   sv->events_used = 0;
   sv->trace.clear();
   return SV_OK;
 }
 
+int sv_trace_start(sv_state *sv) { return sv_trace_start_ex(sv, SV_TRACE_LAUNCHES); }
+
 int sv_trace_stop(sv_state *sv, sv_trace_row *rows, int cap, int *n_rows) {
   if (!sv) return fail(SV_EINVAL, "sv is NULL");
   sv->tracing = false;
+  if (sv->trace_blocks && !sv->trace.empty()) {
+    // close the last block
+    const int e = next_event(sv);
+    if (e < 0) {
+      sv->trace.clear();
+      sv->events_used = 0;
+      return fail(SV_ECUDA, "event creation failed");
+    }
+    PR_CUDA(cudaEventRecord(sv->events[e], sv->stream));
+    sv->trace.back().ev1 = e;
+  }
   PR_CUDA(cudaStreamSynchronize(sv->stream));
   double ms[KN_COUNT] = {0};
   double by[KN_COUNT] = {0};
@@ -73,7 +108,7 @@ int sv_trace_stop(sv_state *sv, sv_trace_row *rows, int cap, int *n_rows) {
     ms[r.name] += t;
     by[r.name] += r.bytes;
     fl[r.name] += r.flops;
-    cnt[r.name] += 1;
+    cnt[r.name] += r.launches;
   }
   int w = 0;
   for (int k = 0; k < KN_COUNT; ++k) {
