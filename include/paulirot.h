@@ -65,6 +65,7 @@ extern "C" {
 #define SV_ECUDA (-3)        /* a CUDA runtime call failed (message has the CUDA error) */
 #define SV_ETIMEOUT (-4)     /* a bounded device wait gave up (batched launch) */
 #define SV_EUNSUPPORTED (-5) /* valid request this build does not handle */
+#define SV_EIO (-6)          /* a checkpoint file could not be written or read, or is corrupt */
 
 /* ---- amplitude types ------------------------------------------------------- */
 #define SV_C128 0 /* complex128: 16 bytes per amplitude, n <= 33 */
@@ -121,6 +122,25 @@ int sv_materialize(sv_state *sv);
 
 /* Copy state and frame of src into dst (same n and dtype). */
 int sv_copy(sv_state *dst, const sv_state *src);
+
+/* ---- checkpoint / resume (not in the paper) -------------------------------------
+ * sv_save writes the amplitudes phi as they lie in device memory, the Pauli
+ * frame Q (the represented state Q phi is restored exactly, nothing is
+ * materialised) and a caller tag (e.g. the index of the next plan of a Trotter
+ * sequence compiled as several plans) to path, through path + ".tmp" renamed
+ * over it, so an existing checkpoint is replaced only by a complete one.  The
+ * file is a 72-byte header (magic "PRCKPT01", version, n, dtype, frame, tag,
+ * sizes, FNV-1a checksums of the amplitudes and of the header) followed by
+ * the amplitudes.  It waits for the handle's stream.  SV_EIO on a file error.
+ *
+ * sv_load reads a checkpoint into a handle of the same n and dtype: SV_EINVAL
+ * if the file is not a checkpoint or its n / dtype differ (nothing changed),
+ * SV_EIO if it is truncated or a checksum fails (header problems change
+ * nothing; an amplitude checksum failure is found after the copy, so the
+ * amplitudes are then unspecified and the frame unchanged).  On success the
+ * frame is the saved one and *out_tag (nullable) the saved tag. */
+int sv_save(sv_state *sv, const char *path, uint64_t tag);
+int sv_load(sv_state *sv, const char *path, uint64_t *out_tag);
 
 /* ---- Pauli frame (host only, O(1) per call) --------------------------------- */
 

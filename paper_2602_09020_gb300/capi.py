@@ -20,7 +20,7 @@ import numpy as np
 
 from . import build as _build
 
-SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_ETIMEOUT, SV_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_ETIMEOUT, SV_EUNSUPPORTED, SV_EIO = 0, -1, -2, -3, -4, -5, -6
 SV_C128, SV_C64 = 0, 1
 _DTYPES = {"c128": SV_C128, "complex128": SV_C128, SV_C128: SV_C128,
            "c64": SV_C64, "complex64": SV_C64, SV_C64: SV_C64}
@@ -71,6 +71,8 @@ def lib() -> ctypes.CDLL:
         "sv_to_host": ([vp, vp, i], i),
         "sv_materialize": ([vp], i),
         "sv_copy": ([vp, vp], i),
+        "sv_save": ([vp, ctypes.c_char_p, u64], i),
+        "sv_load": ([vp, ctypes.c_char_p, P(u64)], i),
         "frame_reset": ([vp], i),
         "frame_apply_pauli": ([vp, ctypes.c_char, i], i),
         "frame_get": ([vp, P(u64), P(u64), P(i)], i),
@@ -123,7 +125,7 @@ def lib() -> ctypes.CDLL:
 def exported_symbols() -> Sequence[str]:
     return ["sv_last_error", "sv_version", "sv_alloc", "sv_wrap", "sv_free", "sv_set_stream",
             "sv_device_ptr", "sv_info", "sv_set_basis_state", "sv_from_host", "sv_to_host",
-            "sv_materialize", "sv_copy", "frame_reset", "frame_apply_pauli", "frame_get",
+            "sv_materialize", "sv_copy", "sv_save", "sv_load", "frame_reset", "frame_apply_pauli", "frame_get",
             "apply_pauli_rotations", "plan_create", "plan_apply", "plan_free", "plan_stats",
             "plan_autotune", "plan_tuned_depth", "plan_set_tuned_depth", "plan_tune_cache_load",
             "plan_tune_cache_save",
@@ -222,6 +224,17 @@ def sv_materialize(sv: int) -> None:
 
 def sv_copy(dst: int, src: int) -> None:
     _check(lib().sv_copy(dst, src))
+
+
+def sv_save(sv: int, path: str, tag: int = 0) -> None:
+    _check(lib().sv_save(sv, os.fsencode(path), ctypes.c_uint64(int(tag))))
+
+
+def sv_load(sv: int, path: str) -> int:
+    """Load a checkpoint into sv (same n and dtype); returns the saved tag."""
+    t = ctypes.c_uint64()
+    _check(lib().sv_load(sv, os.fsencode(path), ctypes.byref(t)))
+    return t.value
 
 
 def frame_reset(sv: int) -> None:
