@@ -321,14 +321,20 @@ def run_ours(a):
         return roof, sum(r[0] for r in rows.values())
 
     # the fusion depth plan_create(-1) takes comes from the library's autotuner,
-    # run on the first Trotter step of the list for each precision (untimed setup)
+    # run on the first Trotter step of the list for each precision (untimed
+    # setup), unless the tune table already holds a depth for (n, dtype) (read
+    # from PAULIROT_TUNE_CACHE, which a tuning run also writes back)
     tuning = {}
     if a.fusion_depth < 0:
         for dt_name in ([a.dtype] if a.skip_extras else [a.dtype, "c128" if a.dtype == "c64" else "c64"]):
+            cached, is_tuned = capi.plan_tuned_depth(a.n, dt_name)
+            if is_tuned:
+                tuning[dt_name] = {"depth": cached, "source": "tune cache"}
+                continue
             svt = capi.sv_alloc(a.n, dt_name, sh)
             t0 = time.perf_counter()
             depth, tms = capi.plan_autotune(svt, rx[:a.terms], rz[:a.terms], rt[:a.terms], reps=2)
-            tuning[dt_name] = {"depth": depth, "tune_s": time.perf_counter() - t0,
+            tuning[dt_name] = {"depth": depth, "source": "autotuned", "tune_s": time.perf_counter() - t0,
                                "sample": f"first {a.terms} rotations",
                                "ms_per_sample_by_depth": {str(d + 1): v for d, v in enumerate(tms) if v > 0}}
             capi.sv_free(svt)
@@ -442,7 +448,8 @@ def run_ours(a):
         "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": a.dtype, "data": "synthetic (seeded JW-shaped Hamiltonian)",
         "config": dict(config_dict(a, a.dtype), fusion_depth=main["dmax"],
-                       fusion_depth_source="autotuned" if a.fusion_depth < 0 else "--fusion-depth"),
+                       fusion_depth_source=(tuning[a.dtype]["source"] if a.fusion_depth < 0
+                                            else "--fusion-depth")),
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
