@@ -89,3 +89,33 @@ def test_autotune_on_a_full_size_state_records_a_depth():
         capi.plan_set_tuned_depth(n, "c64", -1)
         capi.sv_free(sv)
     assert np.all(ms > 0) and depth == int(np.argmin(ms)) + 1
+
+
+def test_tuning_writes_the_cache_named_by_the_environment(tmp_path):
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.txt"
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_2602_09020_gb300 import capi\n"
+        "rng = np.random.default_rng(3)\n"
+        "x = rng.integers(0, 1 << 12, size=40).astype(np.uint64)\n"
+        "z = rng.integers(0, 1 << 12, size=40).astype(np.uint64)\n"
+        "sv = capi.sv_alloc(12, 'c64', torch.cuda.current_stream().cuda_stream)\n"
+        "d, _ = capi.plan_autotune(sv, x, z, rng.uniform(-1, 1, 40), max_depth=3, reps=1)\n"
+        "capi.sv_free(sv)\n"
+        "print(d)\n")
+    env = dict(os.environ, PAULIROT_TUNE_CACHE=str(cache))
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr
+    depth = int(out.stdout.strip())
+    lines = [l.split() for l in cache.read_text().splitlines() if not l.startswith("#")]
+    assert lines == [["c64", "12", str(depth)]]
+    # a second process finds the depth without tuning
+    code2 = "from paper_2602_09020_gb300 import capi\nprint(capi.plan_tuned_depth(12, 'c64'))\n"
+    out = subprocess.run([sys.executable, "-c", code2], cwd=root, env=env, capture_output=True, text=True,
+                         timeout=300)
+    assert out.stdout.strip() == f"({depth}, True)"
