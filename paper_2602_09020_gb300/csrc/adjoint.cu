@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(kThreads)
 // Im<lambda|P|phi> is a sum over amplitudes, and P pairs k with k^x inside any
 // coset of a subspace that contains x.  So a run of consecutive rotations whose
 // x-masks span <= kAdjD dimensions is walked backwards coset by coset: a thread
-// keeps one coset of phi and of lambda in FP64 registers and, for each rotation
+// keeps one coset of phi and of lambda in registers (FP64 for complex128 states,
+// FP32 for complex64, gradient terms always summed in FP64) and, for each rotation
 // of the run (latest first), adds the coset's share of Im<lambda|P_j|phi> to a
 // per-rotation accumulator, then applies R_j^dag (tan form, below) to both.
 // One read and one write of phi and lambda per run instead of per rotation.
@@ -146,20 +147,45 @@ __host__ __device__ constexpr int adj_high_bit(int v) {
   return h;
 }
 
-__device__ __forceinline__ double im_conj_mul(double2 a, double2 b) { return a.x * b.y - a.y * b.x; }  // Im(conj(a) b)
+// Complex registers of the run: double2 for complex128 states; float2 for
+// complex64, whose rotations are applied in FP32 (the precision the state is
+// stored in) while every gradient term is accumulated in FP64.
+template <typename V>
+struct AdjScalar;
+template <>
+struct AdjScalar<double2> {
+  using T = double;
+};
+template <>
+struct AdjScalar<float2> {
+  using T = float;
+};
+template <typename V>
+__device__ __forceinline__ V adj_vec(typename AdjScalar<V>::T x, typename AdjScalar<V>::T y) {
+  V v;
+  v.x = x;
+  v.y = y;
+  return v;
+}
+
+// Im(conj(a) b)
+template <typename V>
+__device__ __forceinline__ typename AdjScalar<V>::T im_conj_mul(V a, V b) {
+  return a.x * b.y - a.y * b.x;
+}
 
 // i^K v, by swaps and negations
-template <int K>
-__device__ __forceinline__ double2 ipow(double2 v) {
+template <int K, typename V>
+__device__ __forceinline__ V ipow(V v) {
   if constexpr ((K & 3) == 0) return v;
-  if constexpr ((K & 3) == 1) return make_double2(-v.y, v.x);
-  if constexpr ((K & 3) == 2) return make_double2(-v.x, -v.y);
-  return make_double2(v.y, -v.x);
+  if constexpr ((K & 3) == 1) return adj_vec<V>(-v.y, v.x);
+  if constexpr ((K & 3) == 2) return adj_vec<V>(-v.x, -v.y);
+  return adj_vec<V>(v.y, -v.x);
 }
 
 // Im(conj(a) i^K b)
-template <int K>
-__device__ __forceinline__ double im_conj_ipow(double2 a, double2 b) {
+template <int K, typename V>
+__device__ __forceinline__ typename AdjScalar<V>::T im_conj_ipow(V a, V b) {
   if constexpr ((K & 3) == 0) return a.x * b.y - a.y * b.x;
   if constexpr ((K & 3) == 1) return a.x * b.x + a.y * b.y;
   if constexpr ((K & 3) == 2) return a.y * b.x - a.x * b.y;
@@ -172,22 +198,25 @@ __device__ __forceinline__ double im_conj_ipow(double2 a, double2 b) {
 //   v_e <- v_e + t (-1)^{sigma_m} i^{K+1} v_m     (R^dag = cos (1 + i t P)),
 // so the phase costs swaps and negations only.  The factor cos(beta/2) is left
 // out: inside a run both vectors carry the same known scale, which the host
-// folds into each gradient and the kernel into the stored states.
-template <int U, int K>
-__device__ __forceinline__ void adj_rot(double2 (&p)[1 << kAdjD], double2 (&l)[1 << kAdjD], const AdjRotDev &r,
-                                        int sig, double &g) {
+// folds into each gradient and the kernel into the stored states.  Each
+// element's gradient term is formed in the state's precision and added to the
+// FP64 accumulator g.
+template <int U, int K, typename V>
+__device__ __forceinline__ void adj_rot(V (&p)[1 << kAdjD], V (&l)[1 << kAdjD], const AdjRotDev &r, int sig,
+                                        double &g) {
+  using S = typename AdjScalar<V>::T;
   constexpr int E = 1 << kAdjD;
-  const double t = r.t;
+  const S t = (S)r.t;
   if constexpr (U == 0) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const bool neg = (sig ^ (int)(r.zt >> e)) & 1;
-      const double ts = neg ? -t : t;
-      const double2 pe = p[e], le = l[e];
-      const double ge = im_conj_mul(le, pe);
-      g += neg ? -ge : ge;
-      p[e] = make_double2(pe.x - ts * pe.y, pe.y + ts * pe.x);
-      l[e] = make_double2(le.x - ts * le.y, le.y + ts * le.x);
+      const S ts = neg ? -t : t;
+      const V pe = p[e], le = l[e];
+      const S ge = im_conj_mul(le, pe);
+      g += (double)(neg ? -ge : ge);
+      p[e] = adj_vec<V>(pe.x - ts * pe.y, pe.y + ts * pe.x);
+      l[e] = adj_vec<V>(le.x - ts * le.y, le.y + ts * le.x);
     }
   } else {
     constexpr int H = adj_high_bit(U);
@@ -196,24 +225,25 @@ __device__ __forceinline__ void adj_rot(double2 (&p)[1 << kAdjD], double2 (&l)[1
       const int e = ((q >> H) << (H + 1)) | (q & ((1 << H) - 1));
       const int m = e ^ U;
       const bool ne = (sig ^ (int)(r.zt >> e)) & 1, nm = (sig ^ (int)(r.zt >> m)) & 1;
-      const double2 pe = p[e], pm = p[m], le = l[e], lm = l[m];
-      const double ge = im_conj_ipow<K>(le, pm), gm = im_conj_ipow<K>(lm, pe);
-      g += (nm ? -ge : ge) + (ne ? -gm : gm);
-      const double te = ne ? -t : t, tm = nm ? -t : t;
-      const double2 wpm = ipow<K + 1>(pm), wpe = ipow<K + 1>(pe), wlm = ipow<K + 1>(lm), wle = ipow<K + 1>(le);
-      p[e] = make_double2(pe.x + tm * wpm.x, pe.y + tm * wpm.y);
-      p[m] = make_double2(pm.x + te * wpe.x, pm.y + te * wpe.y);
-      l[e] = make_double2(le.x + tm * wlm.x, le.y + tm * wlm.y);
-      l[m] = make_double2(lm.x + te * wle.x, lm.y + te * wle.y);
+      const V pe = p[e], pm = p[m], le = l[e], lm = l[m];
+      const S ge = im_conj_ipow<K>(le, pm), gm = im_conj_ipow<K>(lm, pe);
+      g += (double)(nm ? -ge : ge) + (double)(ne ? -gm : gm);
+      const S te = ne ? -t : t, tm = nm ? -t : t;
+      const V wpm = ipow<K + 1>(pm), wpe = ipow<K + 1>(pe), wlm = ipow<K + 1>(lm), wle = ipow<K + 1>(le);
+      p[e] = adj_vec<V>(pe.x + tm * wpm.x, pe.y + tm * wpm.y);
+      p[m] = adj_vec<V>(pm.x + te * wpe.x, pm.y + te * wpe.y);
+      l[e] = adj_vec<V>(le.x + tm * wlm.x, le.y + tm * wlm.y);
+      l[m] = adj_vec<V>(lm.x + te * wle.x, lm.y + te * wle.y);
     }
   }
 }
 
 #define PR_ADJ_CASE(UK) \
-  case UK: adj_rot<((UK) >> 2), ((UK)&3)>(p, l, r, sig, g); break;
+  case UK: adj_rot<((UK) >> 2), ((UK)&3), V>(p, l, r, sig, g); break;
 
-__device__ __forceinline__ void adj_dispatch(int uk, double2 (&p)[1 << kAdjD], double2 (&l)[1 << kAdjD],
-                                             const AdjRotDev &r, int sig, double &g) {
+template <typename V>
+__device__ __forceinline__ void adj_dispatch(int uk, V (&p)[1 << kAdjD], V (&l)[1 << kAdjD], const AdjRotDev &r,
+                                             int sig, double &g) {
   switch (uk) {
     PR_ADJ_CASE(0)
     PR_ADJ_CASE(4) PR_ADJ_CASE(5) PR_ADJ_CASE(6) PR_ADJ_CASE(7)
@@ -244,12 +274,11 @@ __global__ void __launch_bounds__(kThreads)
       const int pv = run.piv[b];
       rep = ((rep >> pv) << (pv + 1)) | (rep & ((1ULL << pv) - 1));
     }
-    double2 p[E], l[E];
+    C p[E], l[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const C pv = phi[rep ^ run.soff[e]], lv = lam[rep ^ run.soff[e]];
-      p[e] = make_double2(pv.x, pv.y);
-      l[e] = make_double2(lv.x, lv.y);
+      p[e] = phi[rep ^ run.soff[e]];
+      l[e] = lam[rep ^ run.soff[e]];
     }
     for (int j = 0; j < count; ++j) {
       const AdjRotDev &r = run.rot[j];
@@ -258,16 +287,11 @@ __global__ void __launch_bounds__(kThreads)
       adj_dispatch(r.u * 4 + r.ny, p, l, r, sig, g);  // x = 0 has nY = 0
       sacc[j][threadIdx.x] += g;
     }
-    const double sc = run.scale;
+    const R sc = (R)run.scale;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      C o;
-      o.x = (R)(sc * p[e].x);
-      o.y = (R)(sc * p[e].y);
-      phi[rep ^ run.soff[e]] = o;
-      o.x = (R)(sc * l[e].x);
-      o.y = (R)(sc * l[e].y);
-      lam[rep ^ run.soff[e]] = o;
+      phi[rep ^ run.soff[e]] = adj_vec<C>(sc * p[e].x, sc * p[e].y);
+      lam[rep ^ run.soff[e]] = adj_vec<C>(sc * l[e].x, sc * l[e].y);
     }
   }
   __syncthreads();
