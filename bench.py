@@ -637,6 +637,11 @@ def adjoint_measure(capi, torch, barrier, n: int = 20, n_rot: int = 500, n_obs: 
             capi.sv_free(sv)
         out[dtype] = {"ms": 1000.0 * el, "gradients_per_s": n_rot / el, "energy": e,
                       "max_abs_grad": float(np.abs(g).max())}
+        if dtype == "c128":
+            e128, g128 = e, g
+        else:
+            out[dtype]["energy_error_vs_c128"] = abs(e - e128)
+            out[dtype]["max_grad_error_vs_c128"] = float(np.abs(g - g128).max())
     return out
 
 
