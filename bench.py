@@ -653,29 +653,22 @@ def batch_measure(capi, torch, stream, sh, barrier, reps: int = 3):
     sh = int(own.cuda_stream)
     wl = synth.batch_workload(64, seed=4)
     lists = [capi.trotter_expand(c.ham.x, c.ham.z, c.ham.c, c.dt, c.steps, 1, False) for c in wl]
-    # fusion depth per state size from the library's autotuner (depth <= 4, the
-    # batched kernel's limit), timed on the first problem of each size
-    depths = {}
-    for circ, (rx, rz, rt) in zip(wl, lists):
-        if circ.n in depths:
-            continue
-        cached, is_tuned = capi.plan_tuned_depth(circ.n, "c64")
-        if is_tuned and cached <= 4:
-            depths[circ.n] = cached
-            continue
-        svt = capi.sv_alloc(circ.n, "c64", sh)
-        depths[circ.n], _ = capi.plan_autotune(svt, rx, rz, rt, max_depth=4, reps=2)
-        capi.sv_free(svt)
     states, plans, total = [], [], 0
-    for circ, (rx, rz, rt) in zip(wl, lists):
-        total += len(rt)
-        sv = capi.sv_alloc(circ.n, "c64", sh)
-        capi.sv_set_basis_state(sv, circ.basis_state)
-        states.append(sv)
-        plans.append(capi.plan_create(circ.n, "c64", rx, rz, rt, -1, sh))
-    out = {"states": len(wl), "rotations": total, "n_range": [min(c.n for c in wl), max(c.n for c in wl)],
-           "fusion_depth_by_n": {str(k): v for k, v in sorted(depths.items())}}
+    out = {"states": len(wl), "n_range": [min(c.n for c in wl), max(c.n for c in wl)]}
     try:
+        for circ in wl:
+            states.append(capi.sv_alloc(circ.n, "c64", sh))
+        # fusion depth from the library's batched autotuner: the persistent
+        # launch itself timed at depths 1..4; the states are its scratch
+        t0 = time.perf_counter()
+        depth, bms = capi.batch_autotune(states, lists, max_depth=4, reps=2)
+        out.update({"fusion_depth": depth, "tune_s": time.perf_counter() - t0,
+                    "ms_per_launch_by_depth": {str(d + 1): v for d, v in enumerate(bms) if v > 0}})
+        for sv, circ, (rx, rz, rt) in zip(states, wl, lists):
+            total += len(rt)
+            capi.sv_set_basis_state(sv, circ.basis_state)
+            plans.append(capi.plan_create(circ.n, "c64", rx, rz, rt, -1, sh))
+        out["rotations"] = total
         capi.batch_run(states, plans, use_graph=True)  # builds, captures, warms
         barrier()
         t0 = time.perf_counter()

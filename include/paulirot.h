@@ -203,6 +203,21 @@ int plan_free(sv_plan *plan);
 int plan_autotune(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *angles, size_t count,
                   int max_depth, int reps, int *out_depth, double *out_ms);
 
+/* Fusion depth for a batched launch (batch_run), timed on the launch itself:
+ * for every depth 1..max_depth (max_depth <= 0 or > 4 means 4, the batched
+ * kernel's limit) each state's list x[i], z[i], angles[i] (counts[i]
+ * rotations) is compiled as by plan_create, the batch is run once untimed and
+ * then reps times (reps <= 0 means 3) with CUDA events on states[0]'s stream
+ * (use_graph as for batch_run).  The fastest depth is recorded for every
+ * (n, dtype) in the batch (replacing single-state entries for those sizes),
+ * so plan_create(-1) compiles for it; ties go to the smaller depth.  The
+ * states are scratch: overwritten.  out_ms (nullable, 4 doubles) receives
+ * the best milliseconds per batched launch for depths 1..4, -1 where not
+ * timed. */
+int batch_autotune(sv_state **states, const uint64_t *const *x, const uint64_t *const *z,
+                   const double *const *angles, const size_t *counts, size_t count, int max_depth, int reps,
+                   int use_graph, int *out_depth, double *out_ms);
+
 /* The depth plan_create(-1) would use for (n, dtype) (capped at n);
  * *out_tuned (nullable) = 1 if it comes from the table, 0 if it is the default. */
 int plan_tuned_depth(int n_qubits, int dtype, int *out_depth, int *out_tuned);

@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
         "plan_stats": ([vp, P(sz), P(sz), P(sz)], i),
         "plan_autotune": ([vp, vp, vp, vp, sz, i, i, P(i), vp], i),
         "plan_tuned_depth": ([i, i, P(i), P(i)], i),
+        "batch_autotune": ([vp, vp, vp, vp, vp, sz, i, i, i, P(i), vp], i),
         "plan_set_tuned_depth": ([i, i, i], i),
         "plan_tune_cache_load": ([ctypes.c_char_p], i),
         "plan_tune_cache_save": ([ctypes.c_char_p], i),
@@ -127,7 +128,7 @@ def exported_symbols() -> Sequence[str]:
             "sv_device_ptr", "sv_info", "sv_set_basis_state", "sv_from_host", "sv_to_host",
             "sv_materialize", "sv_copy", "sv_save", "sv_load", "frame_reset", "frame_apply_pauli", "frame_get",
             "apply_pauli_rotations", "plan_create", "plan_apply", "plan_free", "plan_stats",
-            "plan_autotune", "plan_tuned_depth", "plan_set_tuned_depth", "plan_tune_cache_load",
+            "plan_autotune", "batch_autotune", "plan_tuned_depth", "plan_set_tuned_depth", "plan_tune_cache_load",
             "plan_tune_cache_save",
             "trotter_expand", "expval_pauli_sum", "expval_pauli_sum_noalloc", "apply_pauli_sum", "rotation_grads",
             "apply_pauli_rotations_gates", "batch_run", "batch_run_ex", "batch_info", "sv_trace_start",
@@ -293,6 +294,29 @@ def plan_autotune(sv: int, x, z, angles, max_depth: int = 0, reps: int = 0) -> T
     ms = np.empty(5, np.float64)
     _check(lib().plan_autotune(sv, _p(x), _p(z), _p(a), len(a), int(max_depth), int(reps), ctypes.byref(d),
                                _p(ms)))
+    return d.value, ms
+
+
+def batch_autotune(states, lists, max_depth: int = 4, reps: int = 3, use_graph: bool = True):
+    """Time the batched launch of the lists (one (x, z, angles) per state) at
+    every fusion depth and record the fastest for the states' sizes.  The
+    states are overwritten.  Returns (depth, ms per launch for depths 1..4)."""
+    if len(states) != len(lists) or not states:
+        raise ValueError("one rotation list per state")
+    keep = [(_u64(x), _u64(z), _f64(a)) for x, z, a in lists]
+    for x, z, a in keep:
+        if not (len(x) == len(z) == len(a)):
+            raise ValueError("x, z and angles must have equal length")
+    k = len(states)
+    sv = (ctypes.c_void_p * k)(*states)
+    xp = (ctypes.c_void_p * k)(*[x.ctypes.data for x, _, _ in keep])
+    zp = (ctypes.c_void_p * k)(*[z.ctypes.data for _, z, _ in keep])
+    ap = (ctypes.c_void_p * k)(*[a.ctypes.data for _, _, a in keep])
+    cnt = (ctypes.c_size_t * k)(*[len(a) for _, _, a in keep])
+    d = ctypes.c_int()
+    ms = np.empty(4, np.float64)
+    _check(lib().batch_autotune(sv, xp, zp, ap, cnt, k, int(max_depth), int(reps), int(bool(use_graph)),
+                                ctypes.byref(d), _p(ms)))
     return d.value, ms
 
 

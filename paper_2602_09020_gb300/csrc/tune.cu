@@ -19,6 +19,7 @@
 #include <mutex>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "internal.h"
 
@@ -219,6 +220,81 @@ int plan_autotune(sv_state *sv, const uint64_t *x, const uint64_t *z, const doub
   std::lock_guard<std::mutex> lk(g_mu);
   load_env_locked();
   g_table[Key(sv->dtype, sv->n)] = best;
+  if (const char *p = env_path()) return write_file(p, g_table);
+  return SV_OK;
+}
+
+int batch_autotune(sv_state **states, const uint64_t *const *x, const uint64_t *const *z,
+                   const double *const *angles, const size_t *counts, size_t count, int max_depth, int reps,
+                   int use_graph, int *out_depth, double *out_ms) {
+  constexpr int kBatchDMax = 4;
+  if (!states || !x || !z || !angles || !counts || !out_depth) return fail(SV_EINVAL, "NULL argument");
+  if (count == 0) return fail(SV_EINVAL, "empty batch");
+  for (size_t i = 0; i < count; ++i)
+    if (!states[i]) return fail(SV_EINVAL, "state %zu is NULL", i);
+  if (max_depth <= 0 || max_depth > kBatchDMax) max_depth = kBatchDMax;
+  if (reps <= 0) reps = 3;
+  if (out_ms)
+    for (int d = 0; d < kBatchDMax; ++d) out_ms[d] = -1.0;
+  std::vector<sv_plan *> plans(count * (size_t)max_depth, nullptr);
+  auto release = [&]() {
+    for (sv_plan *p : plans)
+      if (p) plan_free(p);
+  };
+  // compile everything first: a bad list fails before any device work
+  for (int d = 1; d <= max_depth; ++d)
+    for (size_t i = 0; i < count; ++i) {
+      const int dd = d < states[i]->n ? d : states[i]->n;
+      int rc = plan_create(&plans[(size_t)(d - 1) * count + i], states[i]->n, states[i]->dtype, x[i], z[i],
+                           angles[i], counts[i], dd, states[i]->stream);
+      if (rc) {
+        release();
+        return rc;
+      }
+    }
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) {
+    cudaGetLastError();
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    release();
+    return fail(SV_ECUDA, "event creation failed");
+  }
+  cudaStream_t s = states[0]->stream;
+  double best_ms[kBatchDMax];
+  for (int d = 0; d < kBatchDMax; ++d) best_ms[d] = -1.0;
+  int rc = SV_OK;
+  for (int d = 1; d <= max_depth && rc == SV_OK; ++d) {
+    sv_plan **pl = plans.data() + (size_t)(d - 1) * count;
+    rc = batch_run(states, pl, count, use_graph);  // builds (and captures) this set, warms
+    for (int r = 0; r < reps && rc == SV_OK; ++r) {
+      if (cudaEventRecord(ev[0], s) != cudaSuccess) {
+        rc = fail(SV_ECUDA, "event record");
+        break;
+      }
+      rc = batch_run(states, pl, count, use_graph);  // synchronises the stream
+      if (rc) break;
+      if (cudaEventRecord(ev[1], s) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess) {
+        rc = fail(SV_ECUDA, "event wait: %s", cudaGetErrorString(cudaGetLastError()));
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (best_ms[d - 1] < 0.0 || ms < best_ms[d - 1]) best_ms[d - 1] = ms;
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  release();
+  if (rc) return rc;
+  int best = 1;
+  for (int d = 2; d <= max_depth; ++d)
+    if (best_ms[d - 1] < best_ms[best - 1]) best = d;
+  if (out_ms)
+    for (int d = 0; d < kBatchDMax; ++d) out_ms[d] = best_ms[d];
+  *out_depth = best;
+  std::lock_guard<std::mutex> lk(g_mu);
+  load_env_locked();
+  for (size_t i = 0; i < count; ++i) g_table[Key(states[i]->dtype, states[i]->n)] = best;
   if (const char *p = env_path()) return write_file(p, g_table);
   return SV_OK;
 }

@@ -104,3 +104,44 @@ def test_batch_barrier_timeout_reports_and_recovers():
     ref = _run(probs, "c64", stream.cuda_stream, "single")
     for a, b in zip(got, ref):
         np.testing.assert_array_equal(a, b)
+
+
+def test_batch_autotune_records_the_fastest_depth_for_every_size():
+    problems = _problems([10, 11, 12, 12, 16, 18], 40, "c64")
+    stream = torch.cuda.Stream()
+    sh = int(stream.cuda_stream)
+    states = [capi.sv_alloc(n, "c64", sh) for (n, *_rest) in problems]
+    sizes = sorted({p[0] for p in problems})
+    try:
+        depth, ms = capi.batch_autotune(states, [(rx, rz, rt) for (_, rx, rz, rt, _) in problems],
+                                        max_depth=4, reps=2)
+        assert 1 <= depth <= 4 and np.all(ms > 0)
+        assert depth == int(np.argmin(ms)) + 1
+        for n in sizes:
+            assert capi.plan_tuned_depth(n, "c64") == (min(depth, n), True)
+        # the tuned plans run in the batched launch and equal single launches
+        for sv, (n, rx, rz, rt, psi0) in zip(states, problems):
+            capi.sv_from_host(sv, psi0)
+        plans = [capi.plan_create(n, "c64", rx, rz, rt, -1, sh) for (n, rx, rz, rt, _) in problems]
+        try:
+            capi.batch_run(states, plans, use_graph=True)
+            got = [capi.sv_to_host(sv, True) for sv in states]
+            for sv, p, (n, rx, rz, rt, psi0) in zip(states, plans, problems):
+                capi.sv_from_host(sv, psi0)
+                capi.plan_apply(sv, p)
+            want = [capi.sv_to_host(sv, True) for sv in states]
+        finally:
+            for p in plans:
+                capi.plan_free(p)
+        for g, w in zip(got, want):
+            assert g.tobytes() == w.tobytes()
+        with pytest.raises(capi.PauliRotError) as e:
+            capi.batch_autotune(states[:2], [(problems[0][1], problems[0][2], problems[0][3]),
+                                             (problems[1][1][:3], problems[1][2][:3],
+                                              np.array([0.1, np.nan, 0.2]))])
+        assert e.value.code == capi.SV_EINVAL
+    finally:
+        for n in sizes:
+            capi.plan_set_tuned_depth(n, "c64", -1)
+        for sv in states:
+            capi.sv_free(sv)
