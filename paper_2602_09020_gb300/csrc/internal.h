@@ -174,6 +174,9 @@ struct sv_state {
   // work states of rotation_grads (phi and lambda), kept for the next call and
   // released with this handle
   sv_state *work[2] = {nullptr, nullptr};
+  // packed complex64 passes launched on this handle (their parity sets the
+  // direction the next one walks the cosets in)
+  uint32_t packed_passes = 0;
   // tracing
   bool tracing = false;
   bool trace_blocks = false;  // one event per change of kernel instead of per launch

@@ -417,8 +417,12 @@ __host__ __device__ constexpr size_t ws_c64x2() {
 template <typename Idx, int D>
 __device__ __forceinline__ void body_c64x2(float4 *__restrict__ amp4, Idx n_pairs, const RunDev &run,
                                            const RotDev *__restrict__ rots, uint64_t fx, uint64_t fz,
-                                           Idx cta_rank, Idx cta_count, char *ws, bool chained = false) {
+                                           Idx cta_rank, Idx cta_count, char *ws, bool chained = false,
+                                           bool reverse = false) {
   constexpr int E = 1 << D;
+  // reverse: coset pairs are taken from the top (the grid walks them in
+  // descending order), so a pass that follows one in ascending order starts
+  // on the amplitudes its predecessor wrote last, while they are still in L2.
   // chained: launched as a programmatic dependent of the previous pass.  The
   // next pass may be scheduled as this one's CTAs retire; this pass reads its
   // rotation table before waiting for the previous pass, and touches no
@@ -458,13 +462,13 @@ __device__ __forceinline__ void body_c64x2(float4 *__restrict__ amp4, Idx n_pair
   Idx c = cta_rank * blockDim.x + threadIdx.x;
   // prefetch the first coset pair
   if (c < n_pairs) {
-    const Idx rep0 = pair_rep<Idx, D>(c, run);
+    const Idx rep0 = pair_rep<Idx, D>(reverse ? n_pairs - 1 - c : c, run);
 #pragma unroll
     for (int l = 0; l < E; ++l) cp_async16(slot + l * blockDim.x, amp4 + ((rep0 ^ soff[l]) >> 1));
     cp_async_commit();
   }
   for (; c < n_pairs; c += stride) {
-    const Idx rep = pair_rep<Idx, D>(c, run);
+    const Idx rep = pair_rep<Idx, D>(reverse ? n_pairs - 1 - c : c, run);
     cp_async_wait_all();
     float2 RE[E], IM[E];
 #pragma unroll
@@ -482,7 +486,7 @@ __device__ __forceinline__ void body_c64x2(float4 *__restrict__ amp4, Idx n_pair
     // the slot is free again: prefetch the next coset pair while this one computes
     const Idx cn = c + stride;
     if (cn < n_pairs) {
-      const Idx repn = pair_rep<Idx, D>(cn, run);
+      const Idx repn = pair_rep<Idx, D>(reverse ? n_pairs - 1 - cn : cn, run);
 #pragma unroll
       for (int l = 0; l < E; ++l) cp_async16(slot + l * blockDim.x, amp4 + ((repn ^ soff[l]) >> 1));
       cp_async_commit();

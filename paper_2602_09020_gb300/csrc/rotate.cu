@@ -41,9 +41,9 @@ __global__ void __launch_bounds__(kThreads)
 template <typename Idx, int D>
 __global__ void __launch_bounds__(kThreads)
     k_coset_c64x2(float4 *__restrict__ amp4, Idx n_pairs, const __grid_constant__ RunDev run, const RotDev *__restrict__ rots,
-                  uint64_t fx, uint64_t fz) {
+                  uint64_t fx, uint64_t fz, int reverse) {
   extern __shared__ __align__(16) char dyn_ws[];
-  body_c64x2<Idx, D>(amp4, n_pairs, run, rots, fx, fz, (Idx)blockIdx.x, (Idx)gridDim.x, dyn_ws, true);
+  body_c64x2<Idx, D>(amp4, n_pairs, run, rots, fx, fz, (Idx)blockIdx.x, (Idx)gridDim.x, dyn_ws, true, reverse != 0);
 }
 
 template <typename R, typename Idx>
@@ -116,8 +116,11 @@ int launch_c64x2_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  // consecutive packed passes on a state walk the cosets in opposite
+  // directions: the next pass starts where the previous one ended (in L2)
+  const int reverse = (int)(sv->packed_passes++ & 1u);
   PR_CUDA(cudaLaunchKernelEx(&cfg, k_coset_c64x2<Idx, D>, (float4 *)sv->amps, (Idx)n_pairs, run,
-                             (const RotDev *)plan->d_rots, fx, fz));
+                             (const RotDev *)plan->d_rots, fx, fz, reverse));
   trace_end(sv, tr, KN_COSET0 + D, 2.0 * 8.0 * (double)(1ULL << sv->n),
             4.0 * (double)run.count * (double)(1ULL << sv->n));
   return SV_OK;
