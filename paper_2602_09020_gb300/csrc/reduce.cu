@@ -752,7 +752,7 @@ template <typename Idx>
 __global__ void __launch_bounds__(kWThreads, 4)
     k_expval_fix(const float2 *__restrict__ amp, Idx n_tiles, const WhtRunDev run,
                  const WhtGroupDev *__restrict__ ggroups, const WhtTermDev *__restrict__ gterms, int K,
-                 long long *__restrict__ partials) {
+                 long long *__restrict__ partials, int reverse) {
   __shared__ WhtGroupDev groups[kWGroups];
   __shared__ Idx tz[kWTerms];
   __shared__ int tslot[kWTerms];
@@ -776,7 +776,9 @@ __global__ void __launch_bounds__(kWThreads, 4)
   __syncthreads();
   const Idx stride = (Idx)gridDim.x * blockDim.x;
   for (Idx c = (Idx)blockIdx.x * blockDim.x + threadIdx.x; c < n_tiles; c += stride) {
-    Idx rep = c;
+    // consecutive runs read the tiles in opposite orders, so each run starts on
+    // the amplitudes the previous one read last (still in L2)
+    Idx rep = reverse ? n_tiles - 1 - c : c;
 #pragma unroll
     for (int b = 0; b < kWD; ++b) {
       const int pv = run.piv[b];
@@ -1088,7 +1090,7 @@ int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *ener
     const int tr = trace_begin(sv, KN_EXPVAL);
     k_expval_fix<Idx><<<blocks, kWThreads, 0, sv->stream>>>(
         (const float2 *)sv->amps, (Idx)n_tiles, runs[r].dev, (const WhtGroupDev *)base,
-        (const WhtTermDev *)(base + kGroupBytes), 14 - S, part + (size_t)kWTerms * blocks * r);
+        (const WhtTermDev *)(base + kGroupBytes), 14 - S, part + (size_t)kWTerms * blocks * r, (int)((r + 1) & 1));
     PR_CHECK_LAUNCH();
     trace_end(sv, tr, KN_EXPVAL, 8.0 * (double)n_amps);
   }
