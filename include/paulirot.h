@@ -38,6 +38,11 @@
  * failure) and never aborts or exits.  sv_last_error() gives a thread-local
  * message for the last failure on the calling thread.
  *
+ * Threads: a handle (state, plan or Clifford frame) is used by one host
+ * thread at a time.  The library's shared state (tuned fusion depths, the
+ * cached batched launch, phase tables, per-kernel grid sizes) is guarded, so
+ * different handles may be driven from different threads.
+ *
  * Ownership: host arrays passed in are read (or written) before the call
  * returns and stay owned by the caller.  Device memory made by sv_alloc and
  * all internal scratch belong to the library and are released by sv_free.

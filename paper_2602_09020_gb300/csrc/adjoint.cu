@@ -324,15 +324,15 @@ int step_blocks(int n) {
 
 template <typename R>
 int run_blocks_t(int n) {
-  static int cap = 0;
-  if (!cap) {
+  // computed once, on first use (thread-safe static initialisation)
+  static const int cap = [] {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_run<R>, kThreads, 0) != cudaSuccess) {
       cudaGetLastError();
       per_sm = 1;
     }
-    cap = (per_sm > 0 ? per_sm : 1) * device_sm_count();
-  }
+    return (per_sm > 0 ? per_sm : 1) * device_sm_count();
+  }();
   const uint64_t need = (((1ULL << n) >> kAdjD) + kThreads - 1) / kThreads;
   return (int)(need < (uint64_t)cap ? (need ? need : 1) : cap);
 }

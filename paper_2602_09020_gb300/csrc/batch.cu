@@ -12,6 +12,7 @@
 // reports SV_ETIMEOUT.  No wait is unbounded.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <queue>
 #include <vector>
 
@@ -203,6 +204,7 @@ struct BatchCache {
 };
 
 BatchCache g_batch;
+std::mutex g_batch_mu;  // guards g_batch: one batched launch at a time
 
 template <typename R, typename Idx>
 int batch_grid(size_t *ws_out) {
@@ -396,6 +398,7 @@ bool same_set(const BatchCache &b, sv_state **states, sv_plan **plans, size_t co
 
 // drop the cached batch if it refers to a handle that is being freed
 void batch_forget(const sv_state *sv, const sv_plan *plan) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
   BatchCache &b = g_batch;
   bool hit = false;
   for (auto *s : b.states) hit = hit || (sv && s == sv);
@@ -426,6 +429,7 @@ int batch_run_ex(sv_state **states, sv_plan **plans, size_t count, int use_graph
     for (size_t j = 0; j < i; ++j)
       if (states[j]->amps == states[i]->amps) return fail(SV_EINVAL, "state %zu appears twice", i);
   }
+  std::lock_guard<std::mutex> lk(g_batch_mu);
   BatchCache &b = g_batch;
   int rc = SV_OK;
   if (!same_set(b, states, plans, count, opts)) {
@@ -503,6 +507,7 @@ int batch_run(sv_state **states, sv_plan **plans, size_t count, int use_graph) {
 }
 
 int batch_info(int *grid_ctas, int *multi_cta_states, int *graph_used) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
   if (grid_ctas) *grid_ctas = g_batch.grid;
   if (multi_cta_states) *multi_cta_states = g_batch.multi_cta_states;
   // 1 = cooperative launch in a graph, 2 = plain launch in a graph, 0 = no graph;

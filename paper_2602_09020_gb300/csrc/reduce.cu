@@ -461,8 +461,7 @@ template <typename R, typename Idx, int D>
 int run_expval_t(sv_state *sv, const std::vector<HostExpRun> &runs, const std::vector<const ExpGroupDev *> &dg,
                  const std::vector<const ExpTermDev *> &dt, double *energy, double *norm2) {
   using C = typename Cx<R>::T;
-  static int cap = 0;
-  if (!cap) cap = occ_blocks(k_expval<R, Idx, D>);
+  static const int cap = occ_blocks(k_expval<R, Idx, D>);
   const uint64_t n_cosets = (1ULL << sv->n) >> D;
   uint64_t need = (n_cosets + kThreads - 1) / kThreads;
   int blocks = (int)(need < (uint64_t)cap ? need : (uint64_t)cap);
@@ -1020,15 +1019,14 @@ void plan_fix(const sv_state *sv, const uint64_t *x, const uint64_t *z, const do
 
 template <typename Idx>
 int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *energy, double *norm2) {
-  static int cap = 0;
-  if (!cap) {
+  static const int cap = [] {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expval_fix<Idx>, kWThreads, 0) != cudaSuccess) {
       cudaGetLastError();
       per_sm = 1;
     }
-    cap = (per_sm > 0 ? per_sm : 1) * device_sm_count();
-  }
+    return (per_sm > 0 ? per_sm : 1) * device_sm_count();
+  }();
   const uint64_t n_amps = 1ULL << sv->n;
   const uint64_t n_tiles = n_amps >> kWD;
   const uint64_t need = (n_tiles + kWThreads - 1) / kWThreads;
@@ -1149,8 +1147,7 @@ template <typename R, typename Idx, int D>
 static int run_pauli_sum_t(sv_state *dst, sv_state *src, const std::vector<HostExpRun> &runs,
                            const std::vector<const ExpGroupDev *> &dg, const std::vector<const ExpTermDev *> &dt) {
   using C = typename Cx<R>::T;
-  static int cap = 0;
-  if (!cap) cap = occ_blocks(k_pauli_sum<R, Idx, D>);
+  static const int cap = occ_blocks(k_pauli_sum<R, Idx, D>);
   const uint64_t n_cosets = (1ULL << src->n) >> D;
   uint64_t need = (n_cosets + kThreads - 1) / kThreads;
   int blocks = (int)(need < (uint64_t)cap ? need : (uint64_t)cap);

@@ -24,6 +24,8 @@
 // Taylor step for the remaining angle below 2 pi / 2^16.
 #include <cmath>
 
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace pr {
@@ -69,8 +71,7 @@ int occupancy_blocks(K kernel, int threads) {
 template <typename R, typename Idx, int D, int V>
 int launch_coset_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t fx, uint64_t fz) {
   using C = typename Cx<R>::T;
-  static int cap = 0;
-  if (!cap) cap = occupancy_blocks(k_coset<R, Idx, D, V>, kThreads);
+  static const int cap = occupancy_blocks(k_coset<R, Idx, D, V>, kThreads);
   const uint64_t n_cosets = (1ULL << sv->n) >> D;
   uint64_t need = (n_cosets + (uint64_t)kThreads * V - 1) / ((uint64_t)kThreads * V);
   unsigned blocks = (unsigned)(need < (uint64_t)cap ? need : (uint64_t)cap);
@@ -86,17 +87,24 @@ int launch_coset_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_
 
 template <typename Idx, int D>
 int launch_c64x2_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t fx, uint64_t fz) {
-  static int cap = 0;
   const size_t dyn = ws_c64x2<Idx, D>();
-  if (!cap) {
-    PR_CUDA(cudaFuncSetAttribute(k_coset_c64x2<Idx, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  // computed once, on first use (thread-safe static initialisation); -1 if the
+  // kernel's shared-memory size cannot be set
+  static const int cap = [] {
+    const size_t bytes = ws_c64x2<Idx, D>();
+    if (cudaFuncSetAttribute(k_coset_c64x2<Idx, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coset_c64x2<Idx, D>, kThreads, dyn) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coset_c64x2<Idx, D>, kThreads, bytes) != cudaSuccess) {
       cudaGetLastError();
       per_sm = 1;
     }
-    cap = (per_sm > 0 ? per_sm : 1) * device_sm_count();
-  }
+    return (per_sm > 0 ? per_sm : 1) * device_sm_count();
+  }();
+  if (cap < 0) return fail(SV_ECUDA, "cannot set the shared-memory size of the packed pass");
   const uint64_t n_pairs = ((1ULL << sv->n) >> D) >> 1;
   uint64_t need = (n_pairs + kThreads - 1) / kThreads;
   unsigned blocks = (unsigned)(need < (uint64_t)cap ? need : (uint64_t)cap);
@@ -163,8 +171,11 @@ int launch_coset_d(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_
 constexpr int kMaxDevices = 64;
 void *g_tab[kMaxDevices][2];
 
+std::mutex g_tab_mu;
+
 int ensure_tables(int dev, int dtype, const void **out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(SV_EUNSUPPORTED, "device index %d", dev);
+  std::lock_guard<std::mutex> lk(g_tab_mu);
   const int slot = dtype == SV_C128 ? 0 : 1;
   if (!g_tab[dev][slot]) {
     const double two_pi = 6.283185307179586476925286766559;
@@ -202,8 +213,7 @@ int launch_diag_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t
   const void *tab = nullptr;
   int rc = ensure_tables(sv->device, sv->dtype, &tab);
   if (rc) return rc;
-  static int cap = 0;
-  if (!cap) cap = occupancy_blocks(k_diag_sum<R, Idx>, kThreads);
+  static const int cap = occupancy_blocks(k_diag_sum<R, Idx>, kThreads);
   const uint64_t n_groups = (1ULL << sv->n) >> kDiagClassBits;
   uint64_t need = (n_groups + kThreads - 1) / kThreads;
   unsigned blocks = (unsigned)(need < (uint64_t)cap ? need : (uint64_t)cap);
