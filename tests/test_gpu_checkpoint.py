@@ -134,3 +134,20 @@ def test_damaged_and_mismatched_files(tmp_path):
         assert capi.sv_to_host(a, False).tobytes() == before.tobytes()
     finally:
         capi.sv_free(a)
+
+
+def test_single_qubit_checkpoint(tmp_path):
+    stream_ = stream()
+    a = capi.sv_alloc(1, "c64", stream_)
+    b = capi.sv_alloc(1, "c64", stream_)
+    path = str(tmp_path / "one.ckpt")
+    try:
+        capi.sv_from_host(a, np.array([0.6, 0.8j], dtype=np.complex64))
+        capi.frame_apply_pauli(a, "Y", 0)
+        capi.sv_save(a, path, 0)
+        assert os.path.getsize(path) == 72 + 16
+        assert capi.sv_load(b, path) == 0
+        assert capi.sv_to_host(b, True).tobytes() == capi.sv_to_host(a, True).tobytes()
+    finally:
+        capi.sv_free(a)
+        capi.sv_free(b)

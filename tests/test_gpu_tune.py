@@ -119,3 +119,42 @@ def test_tuning_writes_the_cache_named_by_the_environment(tmp_path):
     out = subprocess.run([sys.executable, "-c", code2], cwd=root, env=env, capture_output=True, text=True,
                          timeout=300)
     assert out.stdout.strip() == f"({depth}, True)"
+
+
+def test_autotune_on_states_smaller_than_the_depths(orc):
+    # n = 2: only depths 1 and 2 exist; the tuner's applications still match the oracle
+    n = 2
+    x = np.array([1, 2, 3, 0, 1], dtype=np.uint64)
+    z = np.array([0, 1, 3, 2, 1], dtype=np.uint64)
+    th = np.array([0.3, -1.1, 2.0, 0.7, -2.9])
+    psi = synth.random_state(n, 1)
+    stream = torch.cuda.current_stream().cuda_stream
+    sv = capi.sv_alloc(n, "c128", stream)
+    try:
+        capi.sv_from_host(sv, psi)
+        depth, ms = capi.plan_autotune(sv, x, z, th, reps=1)
+        got = capi.sv_to_host(sv, True)
+        assert capi.plan_tuned_depth(n, "c128") == (depth, True)
+    finally:
+        capi.plan_set_tuned_depth(n, "c128", -1)
+        capi.sv_free(sv)
+    assert depth in (1, 2) and np.all(ms[:2] > 0) and np.all(ms[2:] == -1)
+    for _ in range(2 * (1 + 2 * 1)):
+        orc.apply_rotations(psi, n, x, z, th)
+    assert np.max(np.abs(got - psi)) <= C128_ATOL
+
+
+def test_autotune_rejects_bad_lists_before_device_work():
+    stream = torch.cuda.current_stream().cuda_stream
+    sv = capi.sv_alloc(6, "c64", stream)
+    try:
+        capi.sv_set_basis_state(sv, 5)
+        before = capi.sv_to_host(sv, True)
+        for x, z, th in (([1 << 6], [0], [0.1]), ([1], [0], [np.inf]), ([], [], [])):
+            with pytest.raises(capi.PauliRotError) as e:
+                capi.plan_autotune(sv, x, z, th)
+            assert e.value.code == capi.SV_EINVAL
+        assert capi.sv_to_host(sv, True).tobytes() == before.tobytes()
+        assert capi.plan_tuned_depth(6, "c64") == (4, False)
+    finally:
+        capi.sv_free(sv)
