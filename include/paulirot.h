@@ -233,7 +233,8 @@ int plan_set_tuned_depth(int n_qubits, int dtype, int depth);
 
 /* Merge the entries of a cache file into the table (a missing file is empty;
  * a malformed one is SV_EINVAL and changes nothing), or write the table to a
- * file (through a temporary file renamed over it).  Host only. */
+ * file (through a temporary file of the calling process renamed over it).
+ * Host only. */
 int plan_tune_cache_load(const char *path);
 int plan_tune_cache_save(const char *path);
 

@@ -11,6 +11,8 @@
 // names a file, the table is read from it before the first lookup and written
 // back after every tuning call.  File format: one "<c64|c128> <n> <depth>" line
 // per entry, '#' starts a comment line.
+#include <unistd.h>
+
 #include <cerrno>
 #include <cstdio>
 #include <cstdlib>
@@ -77,9 +79,10 @@ int read_file(const char *path, std::map<Key, int> *out) {
   return SV_OK;
 }
 
-// Write the table to path (through a temporary file renamed over it).
+// Write the table to path (through a temporary file of this process renamed
+// over it, so processes that tune at the same time never mix their writes).
 int write_file(const char *path, const std::map<Key, int> &t) {
-  std::string tmp = std::string(path) + ".tmp";
+  std::string tmp = std::string(path) + ".tmp." + std::to_string((long)getpid());
   FILE *f = std::fopen(tmp.c_str(), "w");
   if (!f) return fail(SV_EINVAL, "cannot write tune cache %s: %s", tmp.c_str(), std::strerror(errno));
   std::fprintf(f, "# fusion depth per (dtype, n): <dtype> <n> <depth>\n");
