@@ -238,6 +238,26 @@ int plan_set_tuned_depth(int n_qubits, int dtype, int depth);
 int plan_tune_cache_load(const char *path);
 int plan_tune_cache_save(const char *path);
 
+/* The runs a plan is made of, computed on the host only (no device work):
+ * the same planning as plan_create with these arguments.  Runs cover the
+ * rotations in list order, identity strings left out: run i holds the next
+ * runs[i].count of them.  kind 0 = fused coset run (one pass; its x-masks
+ * lie in the span of basis[0..d-1], a reduced basis whose vectors' highest set
+ * bits are distinct), kind 1 = diagonal phase-sum run (x = 0 only; d = 0).  A
+ * run may hold no rotation when it only folds the running scale.  At most cap
+ * runs are written; *out_runs (nullable) = all runs, *out_rotations (nullable)
+ * = rotations after dropping identities. */
+typedef struct sv_run_info {
+  int32_t kind;
+  int32_t d;
+  int32_t count;
+  int32_t reserved;
+  uint64_t basis[5];
+} sv_run_info;
+int plan_inspect(int n_qubits, int dtype, const uint64_t *x, const uint64_t *z, const double *angles,
+                 size_t count, int fusion_depth, sv_run_info *runs, size_t cap, size_t *out_runs,
+                 size_t *out_rotations);
+
 /* Plan statistics: number of rotations (after dropping identities), number
  * of fused runs (= HBM passes), of which diagonal phase-sum runs. */
 int plan_stats(const sv_plan *plan, size_t *n_rotations, size_t *n_runs, size_t *n_diag_runs);

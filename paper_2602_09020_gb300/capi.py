@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
         "plan_apply": ([vp, vp], i),
         "plan_free": ([vp], i),
         "plan_stats": ([vp, P(sz), P(sz), P(sz)], i),
+        "plan_inspect": ([i, i, vp, vp, vp, sz, i, vp, sz, P(sz), P(sz)], i),
         "plan_autotune": ([vp, vp, vp, vp, sz, i, i, P(i), vp], i),
         "plan_tuned_depth": ([i, i, P(i), P(i)], i),
         "batch_autotune": ([vp, vp, vp, vp, vp, sz, i, i, i, P(i), vp], i),
@@ -127,7 +128,7 @@ def exported_symbols() -> Sequence[str]:
     return ["sv_last_error", "sv_version", "sv_alloc", "sv_wrap", "sv_free", "sv_set_stream",
             "sv_device_ptr", "sv_info", "sv_set_basis_state", "sv_from_host", "sv_to_host",
             "sv_materialize", "sv_copy", "sv_save", "sv_load", "frame_reset", "frame_apply_pauli", "frame_get",
-            "apply_pauli_rotations", "plan_create", "plan_apply", "plan_free", "plan_stats",
+            "apply_pauli_rotations", "plan_create", "plan_apply", "plan_free", "plan_stats", "plan_inspect",
             "plan_autotune", "batch_autotune", "plan_tuned_depth", "plan_set_tuned_depth", "plan_tune_cache_load",
             "plan_tune_cache_save",
             "trotter_expand", "expval_pauli_sum", "expval_pauli_sum_noalloc", "apply_pauli_sum", "rotation_grads",
@@ -336,6 +337,30 @@ def plan_tune_cache_load(path: str) -> None:
 
 def plan_tune_cache_save(path: str) -> None:
     _check(lib().plan_tune_cache_save(os.fsencode(path)))
+
+
+class RunInfo(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("d", ctypes.c_int32), ("count", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("basis", ctypes.c_uint64 * 5)]
+
+
+def plan_inspect(n_qubits: int, dtype, x, z, angles, fusion_depth: int = -1):
+    """The runs plan_create would build, planned on the host only.  Returns
+    (runs, rotations): runs is a list of (kind, d, count, basis) with kind 0 =
+    fused coset run, 1 = diagonal phase-sum run; rotations = count after
+    dropping identity strings."""
+    x, z, a = _u64(x), _u64(z), _f64(angles)
+    if not (len(x) == len(z) == len(a)):
+        raise ValueError("x, z and angles must have equal length")
+    nr, nrot = ctypes.c_size_t(), ctypes.c_size_t()
+    L = lib()
+    _check(L.plan_inspect(int(n_qubits), dtype_code(dtype), _p(x), _p(z), _p(a), len(a), int(fusion_depth),
+                          None, 0, ctypes.byref(nr), ctypes.byref(nrot)))
+    buf = (RunInfo * max(1, nr.value))()
+    _check(L.plan_inspect(int(n_qubits), dtype_code(dtype), _p(x), _p(z), _p(a), len(a), int(fusion_depth),
+                          buf, nr.value, ctypes.byref(nr), ctypes.byref(nrot)))
+    runs = [(int(r.kind), int(r.d), int(r.count), [int(v) for v in r.basis[:r.d]]) for r in buf[:nr.value]]
+    return runs, nrot.value
 
 
 def trotter_expand(x, z, c, dt: float, steps: int, order: int = 1, merge: bool = False):

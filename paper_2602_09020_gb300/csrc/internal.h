@@ -226,8 +226,9 @@ int launch_set_basis(sv_state *sv, uint64_t k);
 int launch_scale(sv_state *sv, double re, double im);
 
 // plan building (plan.cu)
+// upload = false: plan on the host only (no device allocation, no upload)
 int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *z,
-               const double *theta, size_t count, int fusion_depth, cudaStream_t stream);
+               const double *theta, size_t count, int fusion_depth, cudaStream_t stream, bool upload = true);
 int apply_plan(sv_state *sv, sv_plan *plan);
 int validate_masks(int n, const uint64_t *x, const uint64_t *z, size_t count);
 // tuned fusion depth for (n, dtype), or -1 if none is recorded (tune.cu)

@@ -84,7 +84,7 @@ struct Eff {
 }  // namespace
 
 int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *z,
-               const double *theta, size_t count, int fusion_depth, cudaStream_t stream) {
+               const double *theta, size_t count, int fusion_depth, cudaStream_t stream, bool upload) {
   (void)stream;
   if (n < 1 || n > max_qubits(dtype)) return fail(SV_EINVAL, "bad n_qubits %d", n);
   if (count && (!x || !z || !theta)) return fail(SV_EINVAL, "NULL rotation arrays");
@@ -346,6 +346,7 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
   p->n_effective = items.size();
   p->n_rots = rots.size();
   p->n_diag = diags.size();
+  if (!upload) return SV_OK;
 
   if (!diags.empty()) {
     rc = prepare_tables(dtype);
@@ -421,6 +422,29 @@ int plan_free(sv_plan *plan) {
   if (plan->d_rots) cudaFree(plan->d_rots);
   if (plan->d_diag) cudaFree(plan->d_diag);
   delete plan;
+  return SV_OK;
+}
+
+int plan_inspect(int n_qubits, int dtype, const uint64_t *x, const uint64_t *z, const double *angles,
+                 size_t count, int fusion_depth, sv_run_info *runs, size_t cap, size_t *out_runs,
+                 size_t *out_rotations) {
+  if (dtype != SV_C128 && dtype != SV_C64) return fail(SV_EINVAL, "bad dtype");
+  if (cap && !runs) return fail(SV_EINVAL, "runs is NULL");
+  sv_plan p;
+  int rc = build_plan(&p, n_qubits, dtype, x, z, angles, count, fusion_depth, nullptr, false);
+  if (rc) return rc;
+  for (size_t i = 0; i < p.runs.size() && i < cap; ++i) {
+    const RunDev &r = p.runs[i];
+    sv_run_info &o = runs[i];
+    std::memset(&o, 0, sizeof(o));
+    o.kind = r.kind;
+    o.d = r.kind == 0 ? r.d : 0;
+    o.count = r.count;
+    if (r.kind == 0)
+      for (int b = 0; b < r.d && b < kDMax; ++b) o.basis[b] = r.basis[b];
+  }
+  if (out_runs) *out_runs = p.runs.size();
+  if (out_rotations) *out_rotations = p.n_effective;
   return SV_OK;
 }
 
