@@ -11,6 +11,7 @@
 // word and leaves; its peers see the word or run out of time too, and the host
 // reports SV_ETIMEOUT.  No wait is unbounded.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <queue>
@@ -248,7 +249,14 @@ int enqueue(BatchCache &b, cudaStream_t s) {
   return launch_by_type(b, s);
 }
 
-// Assign work items to CTAs.  cost = amplitudes x passes.
+// Assign work items to CTAs.  cost ~ amplitudes x (rotations + 4 passes): a
+// pass costs about as much as four of its rotations beyond the rotations
+// themselves.  States of n >= 16 whose cost exceeds one CTA's share are split
+// over several CTAs; how many is decided greedily against the largest load
+// per CTA: start from floor(cost / share), then hand out the CTAs left after
+// the single-CTA states' needs one at a time to the state with the largest
+// load per CTA (or take them back from the state whose load per CTA grows
+// least), so no split state ends up far above the average.
 void assign(const std::vector<double> &cost, const std::vector<int> &n, int grid, std::vector<BatchItemDev> &items,
             std::vector<int> &cta_first, int &multi) {
   const size_t S = cost.size();
@@ -256,23 +264,34 @@ void assign(const std::vector<double> &cost, const std::vector<int> &n, int grid
   for (double c : cost) total += c;
   const double share = total / grid;
   std::vector<int> g(S, 1);
-  int used = 0;
   std::vector<size_t> big;
-  for (size_t i = 0; i < S; ++i)
-    if (cost[i] > 1.5 * share && n[i] >= 16) {
+  double small_total = 0.0;
+  for (size_t i = 0; i < S; ++i) {
+    if (cost[i] > share && n[i] >= 16) {
       g[i] = std::max(1, (int)(cost[i] / share));
       big.push_back(i);
-      used += g[i];
+    } else {
+      small_total += cost[i];
     }
-  // keep at least a quarter of the grid for the single-CTA states
-  const int cap = std::max(1, grid - std::max(1, grid / 4));
-  if (used > cap) {
-    double scale = (double)cap / used;
-    used = 0;
-    for (size_t i : big) {
-      g[i] = std::max(1, (int)(g[i] * scale));
-      used += g[i];
-    }
+  }
+  int limit = grid - (small_total > 0.0 ? (int)std::ceil(small_total / share) : 0);
+  limit = std::max(limit, (int)big.size());
+  int used = 0;
+  for (size_t i : big) used += g[i];
+  while (!big.empty() && used < limit) {
+    size_t best = big[0];
+    for (size_t i : big)
+      if (cost[i] / g[i] > cost[best] / g[best]) best = i;
+    ++g[best];
+    ++used;
+  }
+  while (used > limit) {
+    size_t best = S;
+    for (size_t i : big)
+      if (g[i] > 1 && (best == S || cost[i] / (g[i] - 1) < cost[best] / (g[best] - 1))) best = i;
+    if (best == S) break;
+    --g[best];
+    --used;
   }
   std::vector<std::vector<BatchItemDev>> per_cta(grid);
   std::vector<double> load(grid, 0.0);
@@ -355,7 +374,7 @@ int build_cache(BatchCache &b, sv_state **states, sv_plan **plans, size_t count,
     d.tab = tab;
     d.n = states[i]->n;
     d.n_runs = (int)plans[i]->runs.size();
-    cost[i] = (double)(1ULL << states[i]->n) * (double)(d.n_runs + 1);
+    cost[i] = (double)(1ULL << states[i]->n) * ((double)plans[i]->n_effective + 4.0 * (double)(d.n_runs + 1));
     nq[i] = states[i]->n;
   }
   std::vector<BatchItemDev> items;
