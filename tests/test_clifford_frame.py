@@ -215,3 +215,30 @@ def test_bench_gate_stream_reproduces_the_rotations():
     keep = (ham.x | ham.z) != 0
     assert np.array_equal(ox, ham.x[keep]) and np.array_equal(oz, ham.z[keep])
     np.testing.assert_array_equal(ot, 2 * ham.c[keep])
+
+
+def _anti(a, b):
+    return bin((a[0] & b[1]) ^ (a[1] & b[0])).count("1") & 1
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_frame_stays_a_symplectic_basis_after_every_gate(seed):
+    """The entries F(Z_q), F(X_q) keep the Pauli commutation relations of the
+    Z_q, X_q they stand for after every gate: F(Z_i), F(Z_j) commute, F(X_i),
+    F(X_j) commute, and F(Z_i), F(X_j) anticommute exactly when i = j."""
+    n = 6
+    rng = np.random.default_rng(400 + seed)
+    f = capi.cliff_create(n)
+    try:
+        for g in random_circuit(n, 150, rng):
+            capi.cliff_apply_gates(f, [g])
+            ent = [capi.cliff_entry(f, q) for q in range(n)]
+            zs = [(e[0][0], e[0][1]) for e in ent]
+            xs = [(e[1][0], e[1][1]) for e in ent]
+            assert all(e[0][2] in (1, -1) and e[1][2] in (1, -1) for e in ent)
+            for i in range(n):
+                for j in range(n):
+                    assert _anti(zs[i], zs[j]) == 0 and _anti(xs[i], xs[j]) == 0
+                    assert _anti(zs[i], xs[j]) == (1 if i == j else 0)
+    finally:
+        capi.cliff_free(f)
