@@ -77,8 +77,13 @@ def test_no_kernel_writes_outside_the_state(tmp_path, n, dtype):
         g.check("expval")
         capi.sv_materialize(g.sv)
         g.check("materialize")
-        capi.apply_pauli_rotations_gates(g.sv, x[:10], z[:10], th[:10])
-        g.check("gate-decomposed")
+        if n >= 2:  # the gate-decomposed path needs two qubits (SV_EUNSUPPORTED below)
+            capi.apply_pauli_rotations_gates(g.sv, x[:10], z[:10], th[:10])
+            g.check("gate-decomposed")
+        else:
+            with pytest.raises(capi.PauliRotError) as e:
+                capi.apply_pauli_rotations_gates(g.sv, x[:10], z[:10], th[:10])
+            assert e.value.code == capi.SV_EUNSUPPORTED
         capi.cfhs_measure_pauli(g.sv, None, int(x[0]) | 1, int(z[0]), 0.3)
         g.check("measure")
         capi.rotation_grads(g.sv, x[:30], z[:30], th[:30], hx, hz, hc)
