@@ -146,7 +146,7 @@ struct TraceRec {
 // kernel name ids for tracing
 enum KernelId {
   KN_COSET0 = 0, KN_COSET1, KN_COSET2, KN_COSET3, KN_COSET4, KN_COSET5,
-  KN_DIAG_SUM, KN_EXPVAL, KN_FINISH, KN_PAULI_SUM, KN_MATERIALIZE, KN_SET_BASIS, KN_SCALE,
+  KN_DIAG_SUM, KN_EXPVAL, KN_FINISH, KN_PAULI_SUM, KN_MATERIALIZE, KN_SET_BASIS,
   KN_ADJOINT, KN_SUM_ROWS, KN_GATE1, KN_DIAG1, KN_CNOT, KN_PROJECT, KN_COUNT
 };
 }  // namespace pr
@@ -220,10 +220,9 @@ int device_sm_count();
 int launch_run(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t fx, uint64_t fz);
 int prepare_tables(int dtype);
 int table_pointer(int dtype, const void **out);
-// in-place frame application (rotate.cu)
+// basis state and in-place frame application (state.cu)
 int launch_materialize(sv_state *sv, uint64_t x, uint64_t z, int q);
 int launch_set_basis(sv_state *sv, uint64_t k);
-int launch_scale(sv_state *sv, double re, double im);
 
 // plan building (plan.cu)
 // upload = false: plan on the host only (no device allocation, no upload)

@@ -1,5 +1,5 @@
 // Statevector handles, the Pauli frame, host<->device copies and the small
-// single-pass kernels (basis state, frame materialisation, scalar multiply).
+// single-pass kernels (basis state, frame materialisation).
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -136,18 +136,6 @@ __global__ void k_materialize(C *amp, uint64_t n_amps, uint64_t x, uint64_t z, i
   }
 }
 
-template <typename R, typename C>
-__global__ void k_scale(C *amp, uint64_t n_amps, double re, double im) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const R fr = (R)re, fi = (R)im;
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_amps; t += stride) {
-    C a = amp[t], o;
-    o.x = fr * a.x - fi * a.y;
-    o.y = fr * a.y + fi * a.x;
-    amp[t] = o;
-  }
-}
-
 static unsigned grid_for(uint64_t work) {
   uint64_t blocks = (work + kThreads - 1) / kThreads;
   uint64_t cap = (uint64_t)device_sm_count() * 8;
@@ -178,19 +166,6 @@ int launch_materialize(sv_state *sv, uint64_t x, uint64_t z, int q) {
     k_materialize<float, float2><<<g, kThreads, 0, sv->stream>>>((float2 *)sv->amps, n_amps, x, z, q);
   PR_CHECK_LAUNCH();
   trace_end(sv, tr, KN_MATERIALIZE, 2.0 * (double)amp_bytes(sv->dtype) * (double)n_amps);
-  return SV_OK;
-}
-
-int launch_scale(sv_state *sv, double re, double im) {
-  uint64_t n_amps = 1ULL << sv->n;
-  unsigned g = grid_for(n_amps);
-  const int tr = trace_begin(sv, KN_SCALE);
-  if (sv->dtype == SV_C128)
-    k_scale<double, double2><<<g, kThreads, 0, sv->stream>>>((double2 *)sv->amps, n_amps, re, im);
-  else
-    k_scale<float, float2><<<g, kThreads, 0, sv->stream>>>((float2 *)sv->amps, n_amps, re, im);
-  PR_CHECK_LAUNCH();
-  trace_end(sv, tr, KN_SCALE, 2.0 * (double)amp_bytes(sv->dtype) * (double)n_amps);
   return SV_OK;
 }
 
