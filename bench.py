@@ -58,6 +58,9 @@ def parse_args():
     ap.add_argument("--dt", type=float, default=0.05)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--fusion-depth", type=int, default=-1)
+    ap.add_argument("--tour", action="store_true",
+                    help="launch every kernel family once on states larger than L2 and print their "
+                         "event-timed algorithmic bandwidth (for profiler captures), instead of the bench")
     ap.add_argument("--skip-extras", action="store_true",
                     help="only the timed steps (for profiler launch lists)")
     return ap.parse_args()
@@ -699,10 +702,87 @@ def batch_measure(capi, torch, stream, sh, barrier, reps: int = 3):
     return out
 
 
+def run_tour(a) -> int:
+    """Every kernel family once, in one process, on states larger than L2: the
+    complex64 state at n = 25 (256 MB) and the complex128 state at n = 24
+    (256 MB), a 100-term JW Hamiltonian, one first-order step, <H>, frame
+    materialisation, a few gate-decomposed rotations, one Pauli measurement, a
+    50-rotation adjoint gradient, then a 16-state batched launch.  Kernels are
+    timed with the library's per-launch trace (the adjoint's work states record
+    into their owner's trace); the JSON line gives, per kernel, launches, device
+    time per launch and algorithmic bytes per second against the measured HBM
+    copy peak.  A profiler run over the same command adds the DRAM counters."""
+    import torch
+    from paper_2602_09020_gb300 import capi
+    torch.cuda.set_device(0)
+    own = torch.cuda.Stream()
+    sh = int(own.cuda_stream)
+    pk = peaks()
+    out = {"tour": True, "hbm_peak_gbs": pk["hbm_gbs"], "peak_source": pk["source"], "kernels": {}}
+    for dtype, n in (("c64", 25), ("c128", 24)):
+        ham = synth.jw_hamiltonian(n, 100, a.seed)
+        rx, rz, rt = capi.trotter_expand(ham.x, ham.z, ham.c, a.dt, 1, 1, False)
+        ax, az, ath, obs = synth.adjoint_workload(n, 50, 100, seed=a.seed)
+        # one rotation with X and Y parts on three qubits for the gate path
+        gx, gz = np.array([0b10011], dtype=np.uint64), np.array([0b00110], dtype=np.uint64)
+        sv = capi.sv_alloc(n, dtype, sh)
+        plan = capi.plan_create(n, dtype, rx, rz, rt, -1, sh)
+        try:
+            capi.sv_trace_start(sv)
+            capi.sv_set_basis_state(sv, synth.hartree_fock_index(n // 2))
+            capi.plan_apply(sv, plan)
+            capi.expval_pauli_sum(sv, ham.x, ham.z, ham.c)
+            capi.frame_apply_pauli(sv, "Y", 3)
+            capi.sv_materialize(sv)
+            capi.apply_pauli_rotations_gates(sv, gx, gz, [0.3])
+            capi.cfhs_measure_pauli(sv, None, 0b1010, 0b0110, 0.5)
+            capi.rotation_grads(sv, ax, az, ath, obs.x, obs.z, obs.c)
+            rows = capi.sv_trace_stop(sv)
+        finally:
+            capi.plan_free(plan)
+            capi.sv_free(sv)
+        out["kernels"][f"{dtype}_n{n}"] = {
+            k: {"launches": v[0], "us_per_launch": 1000.0 * v[1] / v[0],
+                "algorithmic_gbs": (v[2] / (v[1] / 1000.0) / 1e9) if v[1] else None,
+                "frac_of_hbm": (v[2] / (v[1] / 1000.0) / 1e9 / pk["hbm_gbs"]) if v[1] else None}
+            for k, v in rows.items()}
+    # the batched launch: 16 states, n ~ U{12..22}
+    wl = synth.batch_workload(16, seed=a.seed)
+    states, plans, nbytes = [], [], 0.0
+    try:
+        for c in wl:
+            rx, rz, rt = capi.trotter_expand(c.ham.x, c.ham.z, c.ham.c, c.dt, c.steps, 1, False)
+            sv = capi.sv_alloc(c.n, "c64", sh)
+            capi.sv_set_basis_state(sv, c.basis_state)
+            states.append(sv)
+            plans.append(capi.plan_create(c.n, "c64", rx, rz, rt, 4, sh))
+            nbytes += capi.plan_stats(plans[-1])[1] * 2.0 * 8.0 * (1 << c.n)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(own)
+        capi.batch_run(states, plans, use_graph=False)
+        e1.record(own)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["kernels"]["batched_16_states"] = {"k_batch": {
+            "launches": 1, "us_per_launch": 1000.0 * ms, "algorithmic_gbs": nbytes / (ms / 1000.0) / 1e9,
+            "frac_of_hbm": nbytes / (ms / 1000.0) / 1e9 / pk["hbm_gbs"],
+            "note": "one launch timed with CUDA events around batch_run (the call also uploads the "
+                    "states' frames); bytes = passes x 2 x 8 x 2^n over the states"}}
+    finally:
+        for p in plans:
+            capi.plan_free(p)
+        for sv in states:
+            capi.sv_free(sv)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     a = parse_args()
     if a.impl == "reference":
         return run_reference(a)
+    if a.tour:
+        return run_tour(a)
     return run_ours(a)
 
 

@@ -382,7 +382,8 @@ typedef struct sv_trace_row {
 } sv_trace_row;
 
 /* Start recording a CUDA event pair around every kernel this handle launches
- * (on the handle's stream).  Recording adds two event records per launch. */
+ * (on the handle's stream), including the kernels rotation_grads runs on the
+ * handle's internal work states.  Recording adds two event records per launch. */
 int sv_trace_start(sv_state *sv);
 
 /* Trace modes.  SV_TRACE_LAUNCHES = sv_trace_start.  SV_TRACE_BLOCKS records one

@@ -478,7 +478,10 @@ int rotation_grads(sv_state *psi0, const uint64_t *x, const uint64_t *z, const d
       rc = sv_alloc(&w, psi0->n, psi0->dtype, psi0->stream);
     }
   sv_state *phi = psi0->work[0], *lam = psi0->work[1];
-  if (!rc) phi->stream = lam->stream = psi0->stream;
+  if (!rc) {
+    phi->stream = lam->stream = psi0->stream;
+    phi->trace_owner = lam->trace_owner = psi0;  // a trace of psi0 shows the sweep's kernels
+  }
   const Pauli q0 = psi0->frame;
   if (!rc) rc = sv_copy(phi, psi0);
   if (!rc) rc = apply_plan(phi, plan);

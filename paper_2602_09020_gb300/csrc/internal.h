@@ -174,6 +174,8 @@ struct sv_state {
   // work states of rotation_grads (phi and lambda), kept for the next call and
   // released with this handle
   sv_state *work[2] = {nullptr, nullptr};
+  // a work state records its launches in its owner's trace (null: its own)
+  sv_state *trace_owner = nullptr;
   // packed complex64 passes launched on this handle (their parity sets the
   // direction the next one walks the cosets in)
   uint32_t packed_passes = 0;

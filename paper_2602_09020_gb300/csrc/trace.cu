@@ -26,6 +26,7 @@ static int next_event(sv_state *sv) {
 }
 
 int trace_begin(sv_state *sv, int name) {
+  if (sv && sv->trace_owner) sv = sv->trace_owner;
   if (!sv || !sv->tracing) return -1;
   if (sv->trace_blocks) {
     // one event where the kernel changes: it ends the open block and opens the next
@@ -44,6 +45,7 @@ int trace_begin(sv_state *sv, int name) {
 }
 
 void trace_end(sv_state *sv, int slot, int name, double bytes, double flops) {
+  if (sv && sv->trace_owner) sv = sv->trace_owner;
   if (!sv || !sv->tracing || slot < 0) return;
   if (sv->trace_blocks) {
     TraceRec &r = sv->trace[slot];
