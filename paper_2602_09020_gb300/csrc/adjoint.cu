@@ -425,7 +425,7 @@ int adjoint_runs(sv_state *phi, sv_state *lam, const sv_plan *plan, const Pauli 
       r.row = (int32_t)k;
     }
     run.scale = cprod;
-    const int tr = trace_begin(phi, KN_ADJOINT);
+    const int tr = trace_begin(phi, KN_ADJOINT_RUN);
     if (phi->dtype == SV_C128)
       k_adjoint_run<double><<<blocks, kThreads, 0, phi->stream>>>((double2 *)phi->amps, (double2 *)lam->amps,
                                                                   n_cosets, run, blocks, phi->d_partials);
@@ -433,7 +433,7 @@ int adjoint_runs(sv_state *phi, sv_state *lam, const sv_plan *plan, const Pauli 
       k_adjoint_run<float><<<blocks, kThreads, 0, phi->stream>>>((float2 *)phi->amps, (float2 *)lam->amps,
                                                                  n_cosets, run, blocks, phi->d_partials);
     PR_CHECK_LAUNCH();
-    trace_end(phi, tr, KN_ADJOINT, 4.0 * (double)amp_bytes(phi->dtype) * (double)(1ULL << phi->n));
+    trace_end(phi, tr, KN_ADJOINT_RUN, 4.0 * (double)amp_bytes(phi->dtype) * (double)(1ULL << phi->n));
   }
   return SV_OK;
 }

@@ -147,7 +147,7 @@ struct TraceRec {
 enum KernelId {
   KN_COSET0 = 0, KN_COSET1, KN_COSET2, KN_COSET3, KN_COSET4, KN_COSET5,
   KN_DIAG_SUM, KN_EXPVAL, KN_FINISH, KN_PAULI_SUM, KN_MATERIALIZE, KN_SET_BASIS,
-  KN_ADJOINT, KN_SUM_ROWS, KN_GATE1, KN_DIAG1, KN_CNOT, KN_PROJECT, KN_COUNT
+  KN_ADJOINT, KN_SUM_ROWS, KN_GATE1, KN_DIAG1, KN_CNOT, KN_PROJECT, KN_ADJOINT_RUN, KN_COUNT
 };
 }  // namespace pr
 
