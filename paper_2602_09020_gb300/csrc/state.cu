@@ -103,35 +103,39 @@ __global__ void k_set_one(C *amp, uint64_t k) {
 
 // |phi> <- i^q X^x Z^z |phi>: out_k = i^q (-1)^{popc(z & (k^x))} phi_{k^x}, done
 // pairwise in place over k < k^x (or per element when x = 0).
+// flip the sign bit of v when neg (an integer operation: no FP pipe, exact)
+__device__ __forceinline__ float sign_flip(float v, bool neg) {
+  return __int_as_float(__float_as_int(v) ^ (neg ? (int)0x80000000 : 0));
+}
+__device__ __forceinline__ double sign_flip(double v, bool neg) {
+  return __longlong_as_double(__double_as_longlong(v) ^ (neg ? (long long)0x8000000000000000ULL : 0LL));
+}
+
+// out = i^q (-1)^{popc(k & z)} a: a swap and sign flips, exact
+template <typename R, typename C>
+__device__ __forceinline__ C phase_apply(C a, bool swap, bool negx, bool negy, bool s) {
+  C o;
+  o.x = sign_flip(swap ? a.y : a.x, negx != s);
+  o.y = sign_flip(swap ? a.x : a.y, negy != s);
+  return o;
+}
+
 template <typename R, typename C>
 __global__ void k_materialize(C *amp, uint64_t n_amps, uint64_t x, uint64_t z, int q) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  // i^q as (re, im)
-  const R pre = (q == 0) ? R(1) : (q == 2) ? R(-1) : R(0);
-  const R pim = (q == 1) ? R(1) : (q == 3) ? R(-1) : R(0);
+  // i^q: q = 1 maps (re, im) to (-im, re), q = 2 to (-re, -im), q = 3 to (im, -re)
+  const bool swap = q & 1, negx = q == 1 || q == 2, negy = q == 2 || q == 3;
   const int h = x ? 63 - __clzll((long long)x) : -1;
   const uint64_t work = x ? n_amps >> 1 : n_amps;
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < work; t += stride) {
     if (x == 0) {
-      C a = amp[t];
-      R s = (__popcll(t & z) & 1) ? R(-1) : R(1);
-      C o;
-      o.x = s * (pre * a.x - pim * a.y);
-      o.y = s * (pre * a.y + pim * a.x);
-      amp[t] = o;
+      amp[t] = phase_apply<R>(amp[t], swap, negx, negy, __popcll(t & z) & 1);
     } else {
       uint64_t k = ((t >> h) << (h + 1)) | (t & ((1ULL << h) - 1));
       uint64_t m = k ^ x;
-      C a = amp[k], b = amp[m];
-      R sk = (__popcll(z & m) & 1) ? R(-1) : R(1);  // out_k from phi_m
-      R sm = (__popcll(z & k) & 1) ? R(-1) : R(1);  // out_m from phi_k
-      C ok, om;
-      ok.x = sk * (pre * b.x - pim * b.y);
-      ok.y = sk * (pre * b.y + pim * b.x);
-      om.x = sm * (pre * a.x - pim * a.y);
-      om.y = sm * (pre * a.y + pim * a.x);
-      amp[k] = ok;
-      amp[m] = om;
+      const C a = amp[k], b = amp[m];
+      amp[k] = phase_apply<R>(b, swap, negx, negy, __popcll(z & m) & 1);  // out_k from phi_m
+      amp[m] = phase_apply<R>(a, swap, negx, negy, __popcll(z & k) & 1);  // out_m from phi_k
     }
   }
 }
