@@ -118,7 +118,7 @@ struct ExpTermDev {
 struct ExpGroupDev {
   int32_t u;      // coordinates of the group's x in the run basis
   int32_t first, count;
-  int32_t pad;
+  int32_t pad;    // Hpsi runs: bit 0 = some term has even nY, bit 1 = some has odd nY
 };
 struct ExpRunDev {
   uint64_t basis[kDMax];

@@ -278,8 +278,18 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int q = 1; q < E; ++q)
           if (q == m) am = a[q];
-        o[l].x = fma(cr, am.x, fma(-ci, am.y, o[l].x));
-        o[l].y = fma(cr, am.y, fma(ci, am.x, o[l].y));
+        // groups whose strings all have even (odd) nY have a real (imaginary)
+        // coefficient: half the FP64 multiply-adds
+        if (G.pad == 1) {
+          o[l].x = fma(cr, am.x, o[l].x);
+          o[l].y = fma(cr, am.y, o[l].y);
+        } else if (G.pad == 2) {
+          o[l].x = fma(-ci, am.y, o[l].x);
+          o[l].y = fma(ci, am.x, o[l].y);
+        } else {
+          o[l].x = fma(cr, am.x, fma(-ci, am.y, o[l].x));
+          o[l].y = fma(cr, am.y, fma(ci, am.x, o[l].y));
+        }
       }
     }
 #pragma unroll
@@ -402,6 +412,7 @@ void plan_groups(const sv_state *sv, const uint64_t *x, const uint64_t *z, const
         } else {
           e.coef = t.c;
           e.imag = (uint32_t)ny;
+          G.pad |= (ny & 1) ? 2 : 1;  // the group's coefficient has a real / an imaginary part
         }
         r.terms.push_back(e);
       }
