@@ -84,6 +84,20 @@ class StateVector:
     def copy_from(self, other: "StateVector") -> None:
         capi.sv_copy(self.handle, other.handle)
 
+    # -- checkpoints and tuning
+    def save(self, path: str, tag: int = 0) -> None:
+        """Write the amplitudes, the Pauli frame and tag to path (sv_save)."""
+        capi.sv_save(self.handle, path, tag)
+
+    def load(self, path: str) -> int:
+        """Read a checkpoint of the same n and dtype (sv_load); returns its tag."""
+        return capi.sv_load(self.handle, path)
+
+    def autotune(self, x, z, angles, max_depth: int = 0, reps: int = 0):
+        """Time the list at every fusion depth on this state (overwritten) and
+        record the fastest for its size (plan_autotune); returns (depth, ms)."""
+        return capi.plan_autotune(self.handle, x, z, angles, max_depth, reps)
+
 
 class Plan:
     """A rotation list compiled once (fused runs uploaded to the device)."""

@@ -151,3 +151,29 @@ def test_single_qubit_checkpoint(tmp_path):
     finally:
         capi.sv_free(a)
         capi.sv_free(b)
+
+
+def test_torch_state_vector_checkpoint_and_tuning(tmp_path):
+    from paper_2602_09020_gb300.torch_api import Plan, StateVector
+    n = 12
+    ham = synth.jw_hamiltonian(n, 120, 8)
+    x, z, t = capi.trotter_expand(ham.x, ham.z, ham.c, 0.05, 2, 1, False)
+    a = StateVector(n, "c64")
+    try:
+        depth, ms = a.autotune(x, z, t, max_depth=4, reps=1)
+        assert capi.plan_tuned_depth(n, "c64") == (depth, True)
+        a.set_basis_state(synth.hartree_fock_index(n // 2))
+        plan = Plan(n, "c64", x, z, t)
+        a.apply_plan(plan)
+        a.frame_apply_pauli("X", 2)
+        path = str(tmp_path / "sv.ckpt")
+        a.save(path, tag=5)
+        b = StateVector(n, "c64")
+        assert b.load(path) == 5
+        assert b.frame() == a.frame()
+        assert b.to_host().tobytes() == a.to_host().tobytes()
+        plan.close()
+        b.close()
+    finally:
+        capi.plan_set_tuned_depth(n, "c64", -1)
+        a.close()
