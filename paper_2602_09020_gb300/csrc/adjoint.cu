@@ -168,6 +168,22 @@ __device__ __forceinline__ V adj_vec(typename AdjScalar<V>::T x, typename AdjSca
   return v;
 }
 
+// FP64 value of a gradient term.  For FP32 terms the widening is done with
+// integer operations (rebias the exponent, shift the mantissa: exact for normal
+// numbers and signed zeros), which keeps the FP64 pipe, the kernel's bound,
+// for the sums themselves; subnormals, infinities and NaN take the conversion
+// instruction.
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t e = (b >> 23) & 0xffu;
+  const uint64_t sign = (uint64_t)(b >> 31) << 63;
+  if (e - 1u < 0xfeu)
+    return __longlong_as_double((long long)(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29)));
+  if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
+  return (double)v;
+}
+
 // Im(conj(a) b)
 template <typename V>
 __device__ __forceinline__ typename AdjScalar<V>::T im_conj_mul(V a, V b) {
@@ -214,7 +230,7 @@ __device__ __forceinline__ void adj_rot(V (&p)[1 << kAdjD], V (&l)[1 << kAdjD], 
       const S ts = neg ? -t : t;
       const V pe = p[e], le = l[e];
       const S ge = im_conj_mul(le, pe);
-      g += (double)(neg ? -ge : ge);
+      g += to_f64(neg ? -ge : ge);
       p[e] = adj_vec<V>(pe.x - ts * pe.y, pe.y + ts * pe.x);
       l[e] = adj_vec<V>(le.x - ts * le.y, le.y + ts * le.x);
     }
@@ -227,7 +243,7 @@ __device__ __forceinline__ void adj_rot(V (&p)[1 << kAdjD], V (&l)[1 << kAdjD], 
       const bool ne = (sig ^ (int)(r.zt >> e)) & 1, nm = (sig ^ (int)(r.zt >> m)) & 1;
       const V pe = p[e], pm = p[m], le = l[e], lm = l[m];
       const S ge = im_conj_ipow<K>(le, pm), gm = im_conj_ipow<K>(lm, pe);
-      g += (double)(nm ? -ge : ge) + (double)(ne ? -gm : gm);
+      g += to_f64(nm ? -ge : ge) + to_f64(ne ? -gm : gm);
       const S te = ne ? -t : t, tm = nm ? -t : t;
       const V wpm = ipow<K + 1>(pm), wpe = ipow<K + 1>(pe), wlm = ipow<K + 1>(lm), wle = ipow<K + 1>(le);
       p[e] = adj_vec<V>(pe.x + tm * wpm.x, pe.y + tm * wpm.y);

@@ -126,6 +126,7 @@ struct ExpRunDev {
   int32_t d;
   int32_t n_groups;
   int32_t with_norm;
+  double qscale;  // H psi runs: a term's coefficient is its fixed-point value times qscale
 };
 
 // ---------------------------------------------------------------- host objects

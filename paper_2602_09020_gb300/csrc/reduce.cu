@@ -261,18 +261,23 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
       for (int l = 0; l < E; ++l) {
         const int m = l ^ u;
-        double cr = 0.0, ci = 0.0;  // sum_j c_j i^{nY} s_j(k_m)
+        // sum_j c_j i^{nY} s_j(k_m), exact in 64-bit fixed point (each c_j
+        // is held as round(c_j 2^K), K from the run's sum of |c_j|) on the
+        // integer pipes; one conversion and scale per element and group
+        long long qr = 0, qi = 0;
         for (int j = G.first; j < G.first + G.count; ++j) {
           const ExpTermSm t = terms[j];
           const uint32_t s = (uint32_t)parity((uint64_t)rep & t.z) ^ ((t.zt >> m) & 1u);
-          const double cc = (s & 1u) ? -t.coef : t.coef;
+          const long long q = __double_as_longlong(t.coef);
+          const long long sq = (s & 1u) ? -q : q;
           switch (t.imag & 3u) {
-            case 0: cr += cc; break;
-            case 1: ci += cc; break;
-            case 2: cr -= cc; break;
-            default: ci -= cc; break;
+            case 0: qr += sq; break;
+            case 1: qi += sq; break;
+            case 2: qr -= sq; break;
+            default: qi -= sq; break;
           }
         }
+        const double cr = (double)qr * run.qscale, ci = (double)qi * run.qscale;
         // a[m] read with a runtime index: keep the select explicit
         double2 am = a[0];
 #pragma unroll
@@ -1204,6 +1209,20 @@ int pauli_sum_impl(sv_state *dst, sv_state *src, const uint64_t *x, const uint64
   int D = 0;
   int rc = prepare(src, x, z, c, count, 1, runs, D);
   if (rc) return rc;
+  // coefficients as round(c_j 2^K) with sum_j |c_j| 2^K <= 2^62 over a run, so
+  // every signed partial sum of a group fits in 64 bits; the bits travel in
+  // the coef field
+  for (HostExpRun &r : runs) {
+    double tot = 0.0;
+    for (const ExpTermDev &t : r.terms) tot += std::fabs(t.coef);
+    int K = tot > 0.0 ? 62 - (int)std::ceil(std::log2(tot * (1.0 + 1e-12))) : 0;
+    K = std::max(-960, std::min(960, K));
+    for (ExpTermDev &t : r.terms) {
+      const long long q = std::llround(std::ldexp(t.coef, K));
+      std::memcpy(&t.coef, &q, sizeof(q));
+    }
+    r.dev.qscale = std::ldexp(1.0, -K);
+  }
   std::vector<const ExpGroupDev *> dg;
   std::vector<const ExpTermDev *> dt;
   rc = stage_runs(src, runs, dg, dt);
