@@ -184,6 +184,17 @@ __device__ __forceinline__ double to_f64(float v) {
   return (double)v;
 }
 
+// sum of N values as a tree (depth log2 N): the FP64 adds of one rotation's
+// gradient do not wait on each other in one chain
+template <int N>
+__device__ __forceinline__ double tree_sum(double (&v)[N]) {
+#pragma unroll
+  for (int h = N / 2; h >= 1; h /= 2)
+#pragma unroll
+    for (int i = 0; i < h; ++i) v[i] += v[i + h];
+  return v[0];
+}
+
 // Im(conj(a) b)
 template <typename V>
 __device__ __forceinline__ typename AdjScalar<V>::T im_conj_mul(V a, V b) {
@@ -224,18 +235,21 @@ __device__ __forceinline__ void adj_rot(V (&p)[1 << kAdjD], V (&l)[1 << kAdjD], 
   constexpr int E = 1 << kAdjD;
   const S t = (S)r.t;
   if constexpr (U == 0) {
+    double part[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const bool neg = (sig ^ (int)(r.zt >> e)) & 1;
       const S ts = neg ? -t : t;
       const V pe = p[e], le = l[e];
       const S ge = im_conj_mul(le, pe);
-      g += to_f64(neg ? -ge : ge);
+      part[e] = to_f64(neg ? -ge : ge);
       p[e] = adj_vec<V>(pe.x - ts * pe.y, pe.y + ts * pe.x);
       l[e] = adj_vec<V>(le.x - ts * le.y, le.y + ts * le.x);
     }
+    g += tree_sum(part);
   } else {
     constexpr int H = adj_high_bit(U);
+    double part[E / 2];
 #pragma unroll
     for (int q = 0; q < E / 2; ++q) {
       const int e = ((q >> H) << (H + 1)) | (q & ((1 << H) - 1));
@@ -243,7 +257,7 @@ __device__ __forceinline__ void adj_rot(V (&p)[1 << kAdjD], V (&l)[1 << kAdjD], 
       const bool ne = (sig ^ (int)(r.zt >> e)) & 1, nm = (sig ^ (int)(r.zt >> m)) & 1;
       const V pe = p[e], pm = p[m], le = l[e], lm = l[m];
       const S ge = im_conj_ipow<K>(le, pm), gm = im_conj_ipow<K>(lm, pe);
-      g += to_f64(nm ? -ge : ge) + to_f64(ne ? -gm : gm);
+      part[q] = to_f64(nm ? -ge : ge) + to_f64(ne ? -gm : gm);
       const S te = ne ? -t : t, tm = nm ? -t : t;
       const V wpm = ipow<K + 1>(pm), wpe = ipow<K + 1>(pe), wlm = ipow<K + 1>(lm), wle = ipow<K + 1>(le);
       p[e] = adj_vec<V>(pe.x + tm * wpm.x, pe.y + tm * wpm.y);
@@ -251,6 +265,7 @@ __device__ __forceinline__ void adj_rot(V (&p)[1 << kAdjD], V (&l)[1 << kAdjD], 
       l[e] = adj_vec<V>(le.x + tm * wlm.x, le.y + tm * wlm.y);
       l[m] = adj_vec<V>(lm.x + te * wle.x, lm.y + te * wle.y);
     }
+    g += tree_sum(part);
   }
 }
 
