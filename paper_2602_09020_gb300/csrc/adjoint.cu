@@ -168,20 +168,18 @@ __device__ __forceinline__ V adj_vec(typename AdjScalar<V>::T x, typename AdjSca
   return v;
 }
 
-// FP64 value of a gradient term.  For FP32 terms the widening is done with
-// integer operations (rebias the exponent, shift the mantissa: exact for normal
-// numbers and signed zeros), which keeps the FP64 pipe, the kernel's bound,
-// for the sums themselves; subnormals, infinities and NaN take the conversion
-// instruction.
+// FP64 value of a gradient term.  For FP32 terms the widening is integer work
+// without branches (rebias the exponent, shift the mantissa), which keeps the
+// FP64 pipe, the kernel's bound, for the sums themselves: exact for normal
+// numbers, zeros, infinities and NaN; subnormal terms (below 1.2e-38 in
+// magnitude) count as zero.
 __device__ __forceinline__ double to_f64(double v) { return v; }
 __device__ __forceinline__ double to_f64(float v) {
   const uint32_t b = __float_as_uint(v);
   const uint32_t e = (b >> 23) & 0xffu;
-  const uint64_t sign = (uint64_t)(b >> 31) << 63;
-  if (e - 1u < 0xfeu)
-    return __longlong_as_double((long long)(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29)));
-  if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
-  return (double)v;
+  const uint64_t exp64 = e == 0u ? 0ULL : (e == 0xffu ? 0x7ffULL : (uint64_t)(e + 896u));
+  const uint64_t mant = e == 0u ? 0ULL : (uint64_t)(b & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(((uint64_t)(b >> 31) << 63) | (exp64 << 52) | mant));
 }
 
 // sum of N values as a tree (depth log2 N): the FP64 adds of one rotation's
@@ -295,8 +293,13 @@ __global__ void __launch_bounds__(kThreads)
   using C = typename Cx<R>::T;
   constexpr int E = 1 << kAdjD;
   __shared__ double sacc[kAdjRun][kThreads];  // one column per thread
+  // the run's rotation records in shared memory: read with the loop index
+  // from the kernel parameter they would be indexed constant loads
+  __shared__ AdjRotDev srot[kAdjRun];
   for (int j = 0; j < kAdjRun; ++j) sacc[j][threadIdx.x] = 0.0;
   const int count = run.count;
+  if (threadIdx.x < count) srot[threadIdx.x] = run.rot[threadIdx.x];
+  __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t cs = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; cs < n_cosets; cs += stride) {
     uint64_t rep = cs;
@@ -312,11 +315,19 @@ __global__ void __launch_bounds__(kThreads)
       l[e] = lam[rep ^ run.soff[e]];
     }
     for (int j = 0; j < count; ++j) {
-      const AdjRotDev &r = run.rot[j];
+      const AdjRotDev &r = srot[j];
+      // complex64: the accumulator is read before the rotation's work, so the
+      // load's latency overlaps it instead of stalling the add (complex128
+      // has no register to spare for it)
+      double before = 0.0;
+      if constexpr (sizeof(R) == 4) before = sacc[j][threadIdx.x];
       const int sig = __popcll(rep & r.z) & 1;
       double g = 0.0;
       adj_dispatch(r.u * 4 + r.ny, p, l, r, sig, g);  // x = 0 has nY = 0
-      sacc[j][threadIdx.x] += g;
+      if constexpr (sizeof(R) == 4)
+        sacc[j][threadIdx.x] = before + g;
+      else
+        sacc[j][threadIdx.x] += g;
     }
     const R sc = (R)run.scale;
 #pragma unroll
