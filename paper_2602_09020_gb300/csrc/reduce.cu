@@ -213,6 +213,52 @@ __global__ void k_finish(const double *__restrict__ partials, int n_blocks, doub
 }
 
 // dst += sum_g sum_{j in g} c_j i^{nY_j} s_j(k^x) src_{k^x}   (per element k)
+// One group of an H psi run on a coset: o_l += (sum_j c_j i^{nY_j} s_j(k_m)) a_m
+// with m = l ^ U for every element l.  The coefficient sum is exact in 64-bit
+// fixed point (each c_j held as round(c_j 2^K), K from the run's sum of |c_j|)
+// on the integer pipes: one conversion and scale per element and group.
+template <int U, int E, typename Idx>
+__device__ __forceinline__ void psum_group(const double2 (&a)[E], double2 (&o)[E], const ExpGroupDev &G,
+                                           const ExpTermSm *terms, Idx rep, double qscale) {
+#pragma unroll
+  for (int l = 0; l < E; ++l) {
+    constexpr int UU = U;
+    const int m = l ^ UU;
+    long long qr = 0, qi = 0;
+    for (int j = G.first; j < G.first + G.count; ++j) {
+      const ExpTermSm t = terms[j];
+      const uint32_t s = (uint32_t)parity((uint64_t)rep & t.z) ^ ((t.zt >> m) & 1u);
+      const long long q = __double_as_longlong(t.coef);
+      const long long sq = (s & 1u) ? -q : q;
+      switch (t.imag & 3u) {
+        case 0: qr += sq; break;
+        case 1: qi += sq; break;
+        case 2: qr -= sq; break;
+        default: qi -= sq; break;
+      }
+    }
+    const double cr = (double)qr * qscale, ci = (double)qi * qscale;
+    const double2 am = a[m];
+    // groups whose strings all have even (odd) nY have a real (imaginary)
+    // coefficient: half the FP64 multiply-adds
+    if (G.pad == 1) {
+      o[l].x = fma(cr, am.x, o[l].x);
+      o[l].y = fma(cr, am.y, o[l].y);
+    } else if (G.pad == 2) {
+      o[l].x = fma(-ci, am.y, o[l].x);
+      o[l].y = fma(ci, am.x, o[l].y);
+    } else {
+      o[l].x = fma(cr, am.x, fma(-ci, am.y, o[l].x));
+      o[l].y = fma(cr, am.y, fma(ci, am.x, o[l].y));
+    }
+  }
+}
+
+#define PR_PSUM_CASE(K)                                                  \
+  case K:                                                                \
+    if constexpr ((K) < E) psum_group<(K), E, Idx>(a, o, G, terms, rep, run.qscale); \
+    break;
+
 template <typename R, typename Idx, int D>
 __global__ void __launch_bounds__(kThreads)
     k_pauli_sum(typename Cx<R>::T *__restrict__ dst, const typename Cx<R>::T *__restrict__ src, Idx n_cosets,
@@ -257,44 +303,14 @@ __global__ void __launch_bounds__(kThreads)
     }
     for (int g = 0; g < run.n_groups; ++g) {
       const ExpGroupDev G = sg[g];
-      const int u = G.u;
-#pragma unroll
-      for (int l = 0; l < E; ++l) {
-        const int m = l ^ u;
-        // sum_j c_j i^{nY} s_j(k_m), exact in 64-bit fixed point (each c_j
-        // is held as round(c_j 2^K), K from the run's sum of |c_j|) on the
-        // integer pipes; one conversion and scale per element and group
-        long long qr = 0, qi = 0;
-        for (int j = G.first; j < G.first + G.count; ++j) {
-          const ExpTermSm t = terms[j];
-          const uint32_t s = (uint32_t)parity((uint64_t)rep & t.z) ^ ((t.zt >> m) & 1u);
-          const long long q = __double_as_longlong(t.coef);
-          const long long sq = (s & 1u) ? -q : q;
-          switch (t.imag & 3u) {
-            case 0: qr += sq; break;
-            case 1: qi += sq; break;
-            case 2: qr -= sq; break;
-            default: qi -= sq; break;
-          }
-        }
-        const double cr = (double)qr * run.qscale, ci = (double)qi * run.qscale;
-        // a[m] read with a runtime index: keep the select explicit
-        double2 am = a[0];
-#pragma unroll
-        for (int q = 1; q < E; ++q)
-          if (q == m) am = a[q];
-        // groups whose strings all have even (odd) nY have a real (imaginary)
-        // coefficient: half the FP64 multiply-adds
-        if (G.pad == 1) {
-          o[l].x = fma(cr, am.x, o[l].x);
-          o[l].y = fma(cr, am.y, o[l].y);
-        } else if (G.pad == 2) {
-          o[l].x = fma(-ci, am.y, o[l].x);
-          o[l].y = fma(ci, am.x, o[l].y);
-        } else {
-          o[l].x = fma(cr, am.x, fma(-ci, am.y, o[l].x));
-          o[l].y = fma(cr, am.y, fma(ci, am.x, o[l].y));
-        }
+      // the pairing pattern as a compile-time case: every partner a[l ^ u] is
+      // then a register, not a select over the coset
+      switch (G.u) {
+        PR_PSUM_CASE(0) PR_PSUM_CASE(1) PR_PSUM_CASE(2) PR_PSUM_CASE(3)
+        PR_PSUM_CASE(4) PR_PSUM_CASE(5) PR_PSUM_CASE(6) PR_PSUM_CASE(7)
+        PR_PSUM_CASE(8) PR_PSUM_CASE(9) PR_PSUM_CASE(10) PR_PSUM_CASE(11)
+        PR_PSUM_CASE(12) PR_PSUM_CASE(13) PR_PSUM_CASE(14) PR_PSUM_CASE(15)
+        default: break;
       }
     }
 #pragma unroll
