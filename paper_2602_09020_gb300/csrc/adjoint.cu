@@ -168,20 +168,6 @@ __device__ __forceinline__ V adj_vec(typename AdjScalar<V>::T x, typename AdjSca
   return v;
 }
 
-// FP64 value of a gradient term.  For FP32 terms the widening is integer work
-// without branches (rebias the exponent, shift the mantissa), which keeps the
-// FP64 pipe, the kernel's bound, for the sums themselves: exact for normal
-// numbers, zeros, infinities and NaN; subnormal terms (below 1.2e-38 in
-// magnitude) count as zero.
-__device__ __forceinline__ double to_f64(double v) { return v; }
-__device__ __forceinline__ double to_f64(float v) {
-  const uint32_t b = __float_as_uint(v);
-  const uint32_t e = (b >> 23) & 0xffu;
-  const uint64_t exp64 = e == 0u ? 0ULL : (e == 0xffu ? 0x7ffULL : (uint64_t)(e + 896u));
-  const uint64_t mant = e == 0u ? 0ULL : (uint64_t)(b & 0x7fffffu) << 29;
-  return __longlong_as_double((long long)(((uint64_t)(b >> 31) << 63) | (exp64 << 52) | mant));
-}
-
 // sum of N values as a tree (depth log2 N): the FP64 adds of one rotation's
 // gradient do not wait on each other in one chain
 template <int N>
@@ -240,11 +226,11 @@ __device__ __forceinline__ void adj_rot(V (&p)[1 << kAdjD], V (&l)[1 << kAdjD], 
       const S ts = neg ? -t : t;
       const V pe = p[e], le = l[e];
       const S ge = im_conj_mul(le, pe);
-      part[e] = to_f64(neg ? -ge : ge);
+      part[e] = widen_f64(neg ? -ge : ge);
       p[e] = adj_vec<V>(pe.x - ts * pe.y, pe.y + ts * pe.x);
       l[e] = adj_vec<V>(le.x - ts * le.y, le.y + ts * le.x);
     }
-    g += tree_sum(part);
+    g = tree_sum(part);  // g enters as 0: no add of zero
   } else {
     constexpr int H = adj_high_bit(U);
     double part[E / 2];
@@ -255,7 +241,7 @@ __device__ __forceinline__ void adj_rot(V (&p)[1 << kAdjD], V (&l)[1 << kAdjD], 
       const bool ne = (sig ^ (int)(r.zt >> e)) & 1, nm = (sig ^ (int)(r.zt >> m)) & 1;
       const V pe = p[e], pm = p[m], le = l[e], lm = l[m];
       const S ge = im_conj_ipow<K>(le, pm), gm = im_conj_ipow<K>(lm, pe);
-      part[q] = to_f64(nm ? -ge : ge) + to_f64(ne ? -gm : gm);
+      part[q] = widen_f64(nm ? -ge : ge) + widen_f64(ne ? -gm : gm);
       const S te = ne ? -t : t, tm = nm ? -t : t;
       const V wpm = ipow<K + 1>(pm), wpe = ipow<K + 1>(pe), wlm = ipow<K + 1>(lm), wle = ipow<K + 1>(le);
       p[e] = adj_vec<V>(pe.x + tm * wpm.x, pe.y + tm * wpm.y);
@@ -263,7 +249,7 @@ __device__ __forceinline__ void adj_rot(V (&p)[1 << kAdjD], V (&l)[1 << kAdjD], 
       l[e] = adj_vec<V>(le.x + tm * wlm.x, le.y + tm * wlm.y);
       l[m] = adj_vec<V>(lm.x + te * wle.x, lm.y + te * wle.y);
     }
-    g += tree_sum(part);
+    g = tree_sum(part);  // g enters as 0: no add of zero
   }
 }
 

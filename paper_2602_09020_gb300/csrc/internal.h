@@ -46,6 +46,21 @@ struct Pauli {
 
 inline int popc64(uint64_t v) { return __builtin_popcountll(v); }
 
+#ifdef __CUDACC__
+// FP64 value of an FP32 number by integer work without branches (rebias the
+// exponent, shift the mantissa): exact for normal numbers, zeros, infinities
+// and NaN; subnormals (below 1.2e-38 in magnitude) become zero.  On GB300 the
+// conversion instruction occupies the narrow FP64 pipe as much as an add.
+__device__ __forceinline__ double widen_f64(double v) { return v; }
+__device__ __forceinline__ double widen_f64(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t e = (b >> 23) & 0xffu;
+  const uint64_t exp64 = e == 0u ? 0ULL : (e == 0xffu ? 0x7ffULL : (uint64_t)(e + 896u));
+  const uint64_t mant = e == 0u ? 0ULL : (uint64_t)(b & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(((uint64_t)(b >> 31) << 63) | (exp64 << 52) | mant));
+}
+#endif
+
 // symplectic product: 1 if the two strings anticommute
 inline int anticommute(uint64_t x1, uint64_t z1, uint64_t x2, uint64_t z2) {
   return popc64((x1 & z2) ^ (z1 & x2)) & 1;
