@@ -295,11 +295,11 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int l = 0; l < E; ++l) {
       const C v = src[rep ^ soff[l]];
-      a[l].x = widen_f64(v.x);
-      a[l].y = widen_f64(v.y);
+      a[l].x = (double)v.x;
+      a[l].y = (double)v.y;
       const C w = dst[rep ^ soff[l]];
-      o[l].x = widen_f64(w.x);
-      o[l].y = widen_f64(w.y);
+      o[l].x = (double)w.x;
+      o[l].y = (double)w.y;
     }
     for (int g = 0; g < run.n_groups; ++g) {
       const ExpGroupDev G = sg[g];
