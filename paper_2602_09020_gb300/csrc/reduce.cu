@@ -50,14 +50,64 @@ struct ExpTermSm {
   uint32_t imag;
 };
 
+__host__ __device__ constexpr int adj_high_bit_e(int v) {
+  int h = 0;
+  while (v >> (h + 1)) ++h;
+  return h;
+}
+
+// in-place transform w^[i] = sum_p (-1)^{popc(p & i)} w[p]
+template <int N>
+__device__ __forceinline__ void wht_f64(double (&w)[N]) {
+#pragma unroll
+  for (int h = 1; h < N; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (!(i & h)) {
+        const double x = w[i], y = w[i | h];
+        w[i] = x + y;
+        w[i | h] = x - y;
+      }
+}
+
+// w[i] for a runtime i, as a select over registers (integer work)
+template <int N>
+__device__ __forceinline__ double pick_f64(const double (&w)[N], int i) {
+  double r = w[0];
+#pragma unroll
+  for (int q = 1; q < N; ++q)
+    if (q == i) r = w[q];
+  return r;
+}
+
+// One x-mask group of a <H> run on a coset: acc += sum_j c_j sum_l s_j(l) w_l.
+// Term j's sign at element l is (-1)^{s0_j + zt_j(l)} with zt_j(l) linear in
+// the bits of l (zeta_j: the bits b with zt_j(2^b) = 1), so sum_l (-1)^{zt_j(l)}
+// w_l is entry zeta_j of the Walsh-Hadamard transform of w.  Groups of enough
+// terms take the transform once per coset and then one multiply-add per term
+// (GB300's FP64 pipe is narrow; the index arithmetic and the select are
+// integer work); small groups sum directly.  parts: bit 0 = some term reads
+// the real part of conj(a_l) a_m, bit 1 = the imaginary part (0: both).
 template <int D, int U, typename Idx>
 __device__ __forceinline__ void group_terms(const double2 (&a)[1 << D], Idx rep, const ExpTermSm *terms,
-                                            int first, int count, double &acc) {
+                                            int first, int count, int parts, double &acc) {
   constexpr int E = 1 << D;
   if (U == 0) {
     double p[E];
 #pragma unroll
     for (int l = 0; l < E; ++l) p[l] = a[l].x * a[l].x + a[l].y * a[l].y;
+    if (count >= 5) {
+      wht_f64<E>(p);
+      for (int j = first; j < first + count; ++j) {
+        const ExpTermSm t = terms[j];
+        int zeta = 0;
+#pragma unroll
+        for (int b = 0; b < D; ++b) zeta |= (int)((t.zt >> (1u << b)) & 1u) << b;
+        const double c = parity((uint64_t)rep & t.z) ? -t.coef : t.coef;
+        acc = fma(c, pick_f64<E>(p, zeta), acc);
+      }
+      return;
+    }
     for (int j = first; j < first + count; ++j) {
       const ExpTermSm t = terms[j];
       const uint32_t s0 = (uint32_t)parity((uint64_t)rep & t.z);
@@ -68,6 +118,33 @@ __device__ __forceinline__ void group_terms(const double2 (&a)[1 << D], Idx rep,
       }
     }
   } else {
+    constexpr int H = adj_high_bit_e(U), P = E / 2;
+    if (count >= 4) {
+      // pair values of the leaders l (bit H clear), indexed by l's other bits
+      const bool want_re = parts != 2, want_im = parts != 1;
+      double wr[P], wi[P];
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const int l = ((q >> H) << (H + 1)) | (q & ((1 << H) - 1));
+        const double2 al = a[l], am = a[l ^ U];
+        wr[q] = want_re ? al.x * am.x + al.y * am.y : 0.0;
+        wi[q] = want_im ? al.x * am.y - al.y * am.x : 0.0;
+      }
+      if (want_re) wht_f64<P>(wr);
+      if (want_im) wht_f64<P>(wi);
+      for (int j = first; j < first + count; ++j) {
+        const ExpTermSm t = terms[j];
+        int zeta = 0;
+#pragma unroll
+        for (int k = 0; k < D - 1; ++k) {
+          const int b = k < H ? k : k + 1;
+          zeta |= (int)((t.zt >> (1u << b)) & 1u) << k;
+        }
+        const double c = parity((uint64_t)rep & t.z) ? -t.coef : t.coef;
+        acc = fma(c, t.imag ? pick_f64<P>(wi, zeta) : pick_f64<P>(wr, zeta), acc);
+      }
+      return;
+    }
     double wr[E], wi[E];
 #pragma unroll
     for (int l = 0; l < E; ++l) {
@@ -104,12 +181,12 @@ __device__ __forceinline__ void group_terms(const double2 (&a)[1 << D], Idx rep,
 
 #define PR_GCASE(K) \
   case K:           \
-    if constexpr ((K) < (1 << D)) group_terms<D, (K)>(a, rep, terms, first, count, acc); \
+    if constexpr ((K) < (1 << D)) group_terms<D, (K)>(a, rep, terms, first, count, parts, acc); \
     break;
 
 template <int D, typename Idx>
 __device__ __forceinline__ void group_dispatch(int u, const double2 (&a)[1 << D], Idx rep, const ExpTermSm *terms,
-                                               int first, int count, double &acc) {
+                                               int first, int count, int parts, double &acc) {
   switch (u) {
     PR_GCASE(0) PR_GCASE(1) PR_GCASE(2) PR_GCASE(3) PR_GCASE(4) PR_GCASE(5) PR_GCASE(6) PR_GCASE(7)
     PR_GCASE(8) PR_GCASE(9) PR_GCASE(10) PR_GCASE(11) PR_GCASE(12) PR_GCASE(13) PR_GCASE(14) PR_GCASE(15)
@@ -187,7 +264,11 @@ __global__ void __launch_bounds__(kThreads)
     }
     for (int g = 0; g < run.n_groups; ++g) {
       const ExpGroupDev G = sg[g];
-      group_dispatch<D>(G.u, a, rep, terms, G.first, G.count, acc);
+      // the products depend on the coset only; without this the compiler
+      // hoists every case's products out of the group loop at once
+#pragma unroll
+      for (int l = 0; l < E; ++l) asm volatile("" : "+d"(a[l].x), "+d"(a[l].y));
+      group_dispatch<D>(G.u, a, rep, terms, G.first, G.count, G.pad, acc);
     }
   }
   block_sum2(acc, nrm);
@@ -430,6 +511,7 @@ void plan_groups(const sv_state *sv, const uint64_t *x, const uint64_t *z, const
             e.coef = 2.0 * t.c * ((ny == 0 || ny == 1) ? 1.0 : -1.0);
             e.imag = ny & 1;
           }
+          G.pad |= e.imag ? 2 : 1;  // the group's terms read the real / the imaginary part
         } else {
           e.coef = t.c;
           e.imag = (uint32_t)ny;
