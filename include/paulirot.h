@@ -362,6 +362,16 @@ typedef struct sv_batch_opts {
  * synchronises the stream of states[0] to read the error word. */
 int batch_run_ex(sv_state **states, sv_plan **plans, size_t count, int use_graph, const sv_batch_opts *opts);
 
+/* The batched launch's work assignment, computed on the host only by the rule
+ * batch_run uses: state i has n_qubits[i] qubits and a plan of rotations[i]
+ * rotations in passes[i] passes; the grid has grid_ctas CTAs.  A state's cost
+ * is taken as 2^n (rotations + 4 (passes + 1)); states of n >= 16 costing more than
+ * one CTA's share span several CTAs, the rest are packed onto CTAs.
+ * out_ctas[i] (nullable) = CTAs state i spans (1 when packed with others);
+ * *out_max_over_mean (nullable) = the largest CTA load over the mean load. */
+int batch_inspect(const int *n_qubits, const size_t *rotations, const size_t *passes, size_t count, int grid_ctas,
+                  int *out_ctas, double *out_max_over_mean);
+
 /* Shape of the last batched launch: CTAs in the grid, states that spanned
  * several CTAs, and how it was launched: 1 = cooperative launch replayed from a
  * CUDA graph, 2 = plain launch of the same grid replayed from a graph, 0 = no

@@ -97,6 +97,7 @@ def lib() -> ctypes.CDLL:
         "batch_run": ([vp, vp, sz, i], i),
         "batch_run_ex": ([vp, vp, sz, i, vp], i),
         "batch_info": ([P(i), P(i), P(i)], i),
+        "batch_inspect": ([vp, vp, vp, sz, i, vp, P(d)], i),
         "sv_trace_start": ([vp], i),
         "sv_trace_start_ex": ([vp, i], i),
         "sv_trace_stop": ([vp, vp, i, P(i)], i),
@@ -132,7 +133,7 @@ def exported_symbols() -> Sequence[str]:
             "plan_autotune", "batch_autotune", "plan_tuned_depth", "plan_set_tuned_depth", "plan_tune_cache_load",
             "plan_tune_cache_save",
             "trotter_expand", "expval_pauli_sum", "expval_pauli_sum_noalloc", "apply_pauli_sum", "rotation_grads",
-            "apply_pauli_rotations_gates", "batch_run", "batch_run_ex", "batch_info", "sv_trace_start",
+            "apply_pauli_rotations_gates", "batch_run", "batch_run_ex", "batch_info", "batch_inspect", "sv_trace_start",
             "sv_trace_start_ex", "sv_trace_stop", "cliff_create", "cliff_free", "cliff_reset", "cliff_num_qubits", "cliff_apply_gates",
             "cliff_map_paulis", "cliff_entry", "cliff_is_origin", "cliff_inverse_rotations", "cfhs_apply_gates",
             "cfhs_apply_rotations", "cfhs_expval", "cfhs_materialize", "cfhs_measure_pauli", "cfhs_prepare_qubit"]
@@ -361,6 +362,20 @@ def plan_inspect(n_qubits: int, dtype, x, z, angles, fusion_depth: int = -1):
                           buf, nr.value, ctypes.byref(nr), ctypes.byref(nrot)))
     runs = [(int(r.kind), int(r.d), int(r.count), [int(v) for v in r.basis[:r.d]]) for r in buf[:nr.value]]
     return runs, nrot.value
+
+
+def batch_inspect(n_qubits, rotations, passes, grid_ctas: int):
+    """The batched launch's work assignment on the host: (CTAs per state, the
+    largest CTA load over the mean)."""
+    nq = np.ascontiguousarray(n_qubits, dtype=np.int32)
+    rot = np.ascontiguousarray(rotations, dtype=np.uint64)
+    pas = np.ascontiguousarray(passes, dtype=np.uint64)
+    if not (len(nq) == len(rot) == len(pas)):
+        raise ValueError("one entry per state")
+    ctas = np.empty(len(nq), dtype=np.int32)
+    ratio = ctypes.c_double()
+    _check(lib().batch_inspect(_p(nq), _p(rot), _p(pas), len(nq), int(grid_ctas), _p(ctas), ctypes.byref(ratio)))
+    return ctas, ratio.value
 
 
 def trotter_expand(x, z, c, dt: float, steps: int, order: int = 1, merge: bool = False):

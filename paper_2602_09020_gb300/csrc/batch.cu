@@ -249,6 +249,10 @@ int enqueue(BatchCache &b, cudaStream_t s) {
   return launch_by_type(b, s);
 }
 
+double batch_cost(int n, size_t rotations, size_t passes) {
+  return (double)(1ULL << n) * ((double)rotations + 4.0 * (double)passes);
+}
+
 // Assign work items to CTAs.  cost ~ amplitudes x (rotations + 4 passes): a
 // pass costs about as much as four of its rotations beyond the rotations
 // themselves.  States of n >= 16 whose cost exceeds one CTA's share are split
@@ -374,7 +378,7 @@ int build_cache(BatchCache &b, sv_state **states, sv_plan **plans, size_t count,
     d.tab = tab;
     d.n = states[i]->n;
     d.n_runs = (int)plans[i]->runs.size();
-    cost[i] = (double)(1ULL << states[i]->n) * ((double)plans[i]->n_effective + 4.0 * (double)(d.n_runs + 1));
+    cost[i] = batch_cost(states[i]->n, plans[i]->n_effective, (size_t)d.n_runs + 1);
     nq[i] = states[i]->n;
   }
   std::vector<BatchItemDev> items;
@@ -523,6 +527,38 @@ int batch_run_ex(sv_state **states, sv_plan **plans, size_t count, int use_graph
 
 int batch_run(sv_state **states, sv_plan **plans, size_t count, int use_graph) {
   return batch_run_ex(states, plans, count, use_graph, nullptr);
+}
+
+int batch_inspect(const int *n_qubits, const size_t *rotations, const size_t *passes, size_t count, int grid_ctas,
+                  int *out_ctas, double *out_max_over_mean) {
+  if (count && (!n_qubits || !rotations || !passes)) return fail(SV_EINVAL, "NULL arrays");
+  if (grid_ctas < 1) return fail(SV_EINVAL, "grid_ctas must be >= 1");
+  std::vector<double> cost(count);
+  std::vector<int> nq(count);
+  for (size_t i = 0; i < count; ++i) {
+    if (n_qubits[i] < 1 || n_qubits[i] > 34) return fail(SV_EINVAL, "bad n_qubits %d (state %zu)", n_qubits[i], i);
+    cost[i] = batch_cost(n_qubits[i], rotations[i], passes[i] + 1);
+    nq[i] = n_qubits[i];
+  }
+  std::vector<BatchItemDev> items;
+  std::vector<int> cta_first;
+  int multi = 0;
+  if (count) assign(cost, nq, grid_ctas, items, cta_first, multi);
+  if (out_ctas) {
+    for (size_t i = 0; i < count; ++i) out_ctas[i] = 1;
+    for (const BatchItemDev &it : items) out_ctas[it.state] = it.group;
+  }
+  if (out_max_over_mean) {
+    double total = 0.0, worst = 0.0;
+    for (double c : cost) total += c;
+    for (int c = 0; c < grid_ctas && count; ++c) {
+      double load = 0.0;
+      for (int k = cta_first[c]; k < cta_first[c + 1]; ++k) load += cost[items[k].state] / items[k].group;
+      worst = std::max(worst, load);
+    }
+    *out_max_over_mean = total > 0.0 ? worst / (total / grid_ctas) : 0.0;
+  }
+  return SV_OK;
 }
 
 int batch_info(int *grid_ctas, int *multi_cta_states, int *graph_used) {
