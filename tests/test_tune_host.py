@@ -96,3 +96,26 @@ def test_environment_cache_is_read_before_the_first_lookup(tmp_path):
                          timeout=120)
     assert out.returncode == 0, out.stderr
     assert out.stdout.strip() == "(2, True) (4, True) (4, False)"
+
+
+def test_concurrent_saves_leave_a_whole_cache(tmp_path):
+    """Processes that save the table to one file at the same time each write
+    their own temporary file and rename it over the cache, so the file is
+    always one process's complete table."""
+    path = tmp_path / "shared.txt"
+    code = ("import sys\n"
+            "from paper_2602_09020_gb300 import capi\n"
+            "k = int(sys.argv[1])\n"
+            "for n in range(10, 30):\n"
+            "    capi.plan_set_tuned_depth(n, 'c64', 1 + (n + k) % 5)\n"
+            "for _ in range(50):\n"
+            "    capi.plan_tune_cache_save(sys.argv[2])\n")
+    procs = [subprocess.Popen([sys.executable, "-c", code, str(k), str(path)], cwd=ROOT) for k in range(4)]
+    assert all(p.wait(timeout=120) == 0 for p in procs)
+    lines = [l.split() for l in path.read_text().splitlines() if not l.startswith("#")]
+    assert len(lines) == 20
+    assert sorted(int(n) for _, n, _ in lines) == list(range(10, 30))
+    # one writer's table: every entry follows the same k
+    offs = {(int(d) - 1 - int(n)) % 5 for _, n, d in lines}
+    assert len(offs) == 1
+    assert not list(tmp_path.glob("shared.txt.tmp*"))
