@@ -318,9 +318,14 @@ int apply_pauli_sum(sv_state *dst, sv_state *src, const uint64_t *x, const uint6
  * j, FP64.  Adjoint method: lambda = H psi, then for j = n_rot-1 .. 0:
  * g_j = Im <lambda|P_j|phi_j>, phi <- R_j^dag phi, lambda <- R_j^dag lambda,
  * walked in fused runs (consecutive rotations whose x-masks span <= 3
- * dimensions share one pass over phi and lambda).  The two work states (phi,
- * lambda; psi0's size and type) are allocated on the first call, kept on psi0's
- * handle for later calls and released by sv_free(psi0). */
+ * dimensions share one pass over phi and lambda).  Precision: complex128
+ * computes in FP64; complex64 applies the rotations to phi and lambda in FP32
+ * and sums every gradient term in FP64 (each FP32 term widened exactly; a term
+ * below 1.2e-38 in magnitude counts as zero), and lambda = H psi sums each
+ * element's coefficients exactly in 64-bit fixed point before one FP64
+ * multiply-add per term group.  The two work states (phi, lambda; psi0's size
+ * and type) are allocated on the first call, kept on psi0's handle for later
+ * calls and released by sv_free(psi0). */
 int rotation_grads(sv_state *psi0, const uint64_t *x, const uint64_t *z, const double *angles,
                    size_t n_rot, const uint64_t *hx, const uint64_t *hz, const double *hc,
                    size_t n_terms, double *out_energy, double *out_grads);
