@@ -315,6 +315,70 @@ def test_param_shift_matches_finite_differences(orc):
         assert abs((ep - em) / (2 * h) - grads[j]) < 1e-7 * max(1.0, abs(grads[j]))
 
 
+# ---------------------------------------------------------------- circuits with interleaved Pauli gates
+
+def _dense_circuit(circ):
+    """The circuit as a dense product: the Trotter rotations (Eq. trotter, theta
+    = 2 c dt) in list order, and a gate (position p, Pauli, qubit) applied once
+    the first p rotations have acted (the Circuit convention).  Gates at one
+    position act in the order they are listed."""
+    n = circ.n
+    hx, hz, hc = circ.ham.x, circ.ham.z, circ.ham.c
+    if circ.order != 1:
+        raise ValueError("first-order circuits only")
+    rots = [(int(a), int(b), 2.0 * float(c) * circ.dt) for a, b, c in zip(hx, hz, hc)] * circ.steps
+    masks = {"X": (1, 0), "Y": (1, 1), "Z": (0, 1)}
+    psi = np.zeros(1 << n, dtype=complex)
+    psi[circ.basis_state] = 1.0
+    for p in range(len(rots) + 1):
+        for pos, kind, q in circ.gates:
+            if pos == p:
+                xb, zb = masks[kind]
+                psi = dense.pauli(n, xb << q, zb << q) @ psi
+        if p < len(rots):
+            psi = dense.rotation(n, *rots[p]) @ psi
+    return psi
+
+
+def test_run_circuit_matches_dense_gate_placement(orc):
+    """Pauli gates interleaved with rotations (the CFHS gate-flow workflow: gates
+    and rotations act in stream order) against a dense product, with gates at the
+    first and last insertion points and two at one position.  A gate moved one
+    rotation later, a wrong Pauli or a swapped pair at one position fails."""
+    n = 5
+    g = np.random.default_rng(77)
+    T = 9
+    x = g.integers(0, 1 << n, size=T).astype(np.uint64)
+    z = g.integers(0, 1 << n, size=T).astype(np.uint64)
+    x[0] |= 1  # no pure identity, and a non-diagonal first rotation
+    x[3] |= 2  # the Z gate on qubit 1 at position 3 anticommutes with rotation 3
+    ham = synth.PauliSum(n, x, z, g.uniform(-1.0, 1.0, size=T))
+    L = 2 * T  # two first-order steps
+    gates = [(0, "Y", 2), (0, "X", 0), (3, "Z", 1), (T, "Y", 4), (T + 1, "X", 3), (L, "Z", 0), (L, "Y", 1)]
+    circ = synth.Circuit(n=n, ham=ham, dt=0.37, steps=2, order=1, gates=gates, basis_state=0b00101)
+    want = _dense_circuit(circ)
+    got = orc.run_circuit(circ)
+    np.testing.assert_allclose(got, want, atol=1e-13, rtol=0)
+    kind, sx, sz, st = orc.circuit_sequence(circ)
+    assert len(kind) == L + len(gates) and int(kind.sum()) == len(gates)
+    assert list(kind[:3]) == [1, 1, 0] and list(kind[-3:]) == [0, 1, 1]
+    # moving one gate one rotation later changes the state (the check is sensitive)
+    moved = synth.Circuit(n=n, ham=ham, dt=0.37, steps=2, order=1,
+                          gates=[(4 if p == 3 else p, k, q) for p, k, q in gates], basis_state=0b00101)
+    assert np.max(np.abs(_dense_circuit(moved) - want)) > 1e-3
+
+
+def test_run_circuit_small_workload_recipe_against_dense(orc):
+    """The small workload's recipe (JW-shaped terms, one first-order step at
+    dt = 0.1, 5 seeded Pauli gates at uniform gaps, Hartree-Fock state) at
+    n = 6, where the dense product is cheap."""
+    ham = synth.small_jw_hamiltonian(6, 6, 4, 3)
+    sub = synth.Circuit(n=6, ham=ham, dt=0.1, steps=1, order=1,
+                        gates=synth.random_pauli_gates(6, 5, len(ham) + 1, 4),
+                        basis_state=synth.hartree_fock_index(3))
+    np.testing.assert_allclose(orc.run_circuit(sub), _dense_circuit(sub), atol=1e-13, rtol=0)
+
+
 # ---------------------------------------------------------------- the generators (inputs, not arithmetic)
 
 def test_generators_are_seeded_and_well_formed():
