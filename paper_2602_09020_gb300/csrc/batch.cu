@@ -17,6 +17,7 @@
 #include <queue>
 #include <vector>
 
+#include "coset_fx.cuh"
 #include "kernels.cuh"
 
 namespace pr {
@@ -105,15 +106,26 @@ __device__ void run_pass(const BatchStateDev &st, const RunDev &run, Idx rank, I
       }
     }
   }
-  constexpr bool dbl = sizeof(R) == 8;
-  C *a = (C *)st.amps;
   const Idx nc = (Idx)(n_amps >> run.d);
-  switch (run.d) {
-    case 0: body_coset<R, Idx, 0, dbl ? 2 : 4>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
-    case 1: body_coset<R, Idx, 1, dbl ? 1 : 2>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
-    case 2: body_coset<R, Idx, 2, 1>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
-    case 3: body_coset<R, Idx, 3, 1>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
-    default: body_coset<R, Idx, 4, 1>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
+  if constexpr (sizeof(R) == 8) {
+    // complex128: the fixed-point body of the single-state passes (same results bit for bit)
+    double2 *a = (double2 *)st.amps;
+    switch (run.d) {
+      case 0: body_coset_fx<Idx, 0, 2>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
+      case 1: body_coset_fx<Idx, 1, 1>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
+      case 2: body_coset_fx<Idx, 2, 1>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
+      case 3: body_coset_fx<Idx, 3, 1>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
+      default: body_coset_fx<Idx, 4, 1>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
+    }
+  } else {
+    C *a = (C *)st.amps;
+    switch (run.d) {
+      case 0: body_coset<R, Idx, 0, 4>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
+      case 1: body_coset<R, Idx, 1, 2>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
+      case 2: body_coset<R, Idx, 2, 1>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
+      case 3: body_coset<R, Idx, 3, 1>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
+      default: body_coset<R, Idx, 4, 1>(a, nc, run, st.rots, st.fx, st.fz, rank, group, ws); return;
+    }
   }
 }
 
@@ -152,7 +164,7 @@ constexpr size_t batch_ws() {
     size_t a = ws_c64x2<Idx, 4>(), b = ws_coset<R, Idx, 4>(), c = ws_diag<R, Idx>();
     return std::max(a, std::max(b, c));
   } else {
-    return std::max(ws_coset<R, Idx, 4>(), ws_diag<R, Idx>());
+    return std::max(ws_coset_fx<Idx, 4>(), ws_diag<R, Idx>());
   }
 }
 

@@ -1,0 +1,352 @@
+// Complex128 fused coset pass in 64-bit fixed point on the integer pipes.
+//
+// The pass applies the same tan-form pair update as body_coset (paper, App.
+// "Amplitude update rule for multi-qubit rotations": the 2x2 update of a pair
+// (k, k ^ x); here a_k += t * kappa * (-1)^{popc(k&z)} * a_{k^x} with the
+// positive factor cos(theta/2) left to the plan's running scale), but it does
+// the arithmetic on the integer pipes instead of GB300's narrow FP64 pipe.
+//
+// Representation.  A thread owns one coset of the run's x-span (2^D complex
+// elements, closed under every pairing of the run).  On load every component
+// becomes a signed integer A = round(a * 2^S) with one exponent S per coset:
+// block floating point, S chosen from the largest exponent in the coset so
+// that every component stays below 2^61 for the whole run.  That bound holds
+// because the tan-form step I - i t P multiplies the coset's 2-norm by exactly
+// sqrt(1 + t^2) (P restricted to the coset is a Hermitian involution), and a
+// component never exceeds the coset's 2-norm: the norm grows by a known
+// amount, and whenever the running growth passes a whole bit every component
+// is halved (S decreases by one), so between halvings the growth stays below
+// one bit of headroom.
+//
+// Products.  t is held as T = round(t * 2^62) (|t| < 1 after the planner's
+// angle reduction, T clamped to |T| < 2^62) split as T = th * 2^31 + tl with
+// 0 <= tl < 2^31, and likewise A = ah * 2^31 + al; then
+//   A T / 2^62 = ah th + (ah tl + al th) / 2^31 + al tl / 2^62,
+// three 32 x 32 -> 64-bit integer multiply-adds (fx_madd, fx_msub).  The last term (in [0, 1))
+// is replaced by its mean together with the rounding of the shift, so a
+// product is within 1.25 units of 2^-S of the exact one and unbiased.  Per
+// coset the resolution is 2^-58 of the largest component or finer, which is
+// finer than the 2^-53 relative rounding of the FP64 value the pass stores.
+//
+// Conversions use the IEEE-754 binary64 layout directly (sign, 11-bit biased
+// exponent, 52-bit fraction with an implicit leading one), so no conversion
+// instruction runs on the FP64 pipe: values below 2^-1022 in magnitude
+// (subnormals) are read as zero and results below it are written as zero.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace pr {
+
+namespace {
+
+template <typename Idx>
+struct RotFx {
+  Idx z;
+  uint32_t zt;
+  uint32_t code;
+  int32_t th[2];  // high limbs of +T and -T
+  int32_t tl[2];  // low limbs of +T and -T, in [0, 2^31)
+  int32_t halve;  // 1: halve every component after this rotation
+};
+
+constexpr double kTwo62 = 4611686018427387904.0;  // 2^62
+constexpr int64_t kTMax = (int64_t(1) << 62) - 1;
+// growth bound of one rotation in units of 2^-20 bit
+constexpr int kGrowthFrac = 20;
+
+__device__ __forceinline__ void fx_limbs(int64_t T, int32_t &th, int32_t &tl) {
+  th = (int32_t)(T >> 31);
+  tl = (int32_t)(T & 0x7fffffffLL);
+}
+
+// acc + B * T / 2^62 and acc - B * T / 2^62 for |B| < 2^61 and T = th * 2^31 + tl,
+// 0 <= tl < 2^31: with B = bh * 2^31 + bl (0 <= bl < 2^31),
+//   B T / 2^62 = bh th + (bh tl + bl th) / 2^31 + bl tl / 2^62.
+// The middle sum gets 3 * 2^29 (the mean of the dropped last term, 1/4, plus
+// the shift's floor, 1/2) before its arithmetic shift.  Written as PTX so that
+// each partial product is one 32 x 32 -> 64-bit multiply-add (mad.wide.s32).
+__device__ __forceinline__ int64_t fx_madd(int64_t acc, int64_t b, int32_t th, int32_t tl, int64_t bias) {
+  int64_t r;
+  asm("{\n\t"
+      ".reg .b32 bl, bh, ml, mh;\n\t"
+      ".reg .b64 m;\n\t"
+      "mov.b64 {bl, bh}, %1;\n\t"
+      "shf.r.clamp.b32 bh, bl, bh, 31;\n\t"
+      "and.b32 bl, bl, 0x7fffffff;\n\t"
+      "mad.wide.s32 m, bh, %3, %5;\n\t"
+      "mad.wide.s32 m, bl, %2, m;\n\t"
+      "mov.b64 {ml, mh}, m;\n\t"
+      "shf.r.clamp.b32 ml, ml, mh, 31;\n\t"
+      "shr.s32 mh, mh, 31;\n\t"
+      "mov.b64 m, {ml, mh};\n\t"
+      "add.s64 m, m, %4;\n\t"
+      "mad.wide.s32 %0, bh, %2, m;\n\t"
+      "}"
+      : "=l"(r)
+      : "l"(b), "r"(th), "r"(tl), "l"(acc), "l"(bias));
+  return r;
+}
+
+__device__ __forceinline__ int64_t fx_msub(int64_t acc, int64_t b, int32_t th, int32_t tl, int64_t bias) {
+  int64_t r;
+  asm("{\n\t"
+      ".reg .b32 bl, bh, ml, mh;\n\t"
+      ".reg .b64 m;\n\t"
+      "mov.b64 {bl, bh}, %1;\n\t"
+      "shf.r.clamp.b32 bh, bl, bh, 31;\n\t"
+      "and.b32 bl, bl, 0x7fffffff;\n\t"
+      "mad.wide.s32 m, bh, %3, %5;\n\t"
+      "mad.wide.s32 m, bl, %2, m;\n\t"
+      "mov.b64 {ml, mh}, m;\n\t"
+      "shf.r.clamp.b32 ml, ml, mh, 31;\n\t"
+      "shr.s32 mh, mh, 31;\n\t"
+      "mov.b64 m, {ml, mh};\n\t"
+      "sub.s64 m, %4, m;\n\t"
+      "neg.s32 bh, bh;\n\t"
+      "mad.wide.s32 %0, bh, %2, m;\n\t"
+      "}"
+      : "=l"(r)
+      : "l"(b), "r"(th), "r"(tl), "l"(acc), "l"(bias));
+  return r;
+}
+
+// binary64 -> A = round(a * 2^S), with kbase = 1085 - S; needs 1085 - S - e >= 2
+// for every exponent field e of the coset (guaranteed by the choice of S)
+__device__ __forceinline__ int64_t fx_in(double a, int kbase) {
+  const uint64_t b = (uint64_t)__double_as_longlong(a);
+  const int e = (int)((b >> 52) & 0x7ffu);
+  const int k = kbase - e;  // >= 2
+  const int ks = k < 63 ? k : 63;
+  const uint64_t m10 = ((b & 0xfffffffffffffULL) | 0x10000000000000ULL) << 10;  // < 2^63
+  uint64_t mag = (m10 + (1ULL << (ks - 1))) >> ks;
+  mag = (k < 64 && e != 0) ? mag : 0ULL;
+  return (b >> 63) ? -(int64_t)mag : (int64_t)mag;
+}
+
+// A * 2^-S -> binary64 (rounded to nearest, ties away from zero), ebase = 1086 - S
+__device__ __forceinline__ double fx_out(int64_t a, int ebase) {
+  const uint64_t v = a < 0 ? (uint64_t)(-a) : (uint64_t)a;
+  const int lz = __clzll((long long)v);
+  const uint64_t nm = v << (lz & 63);  // leading one at bit 63
+  const uint64_t m53 = (nm >> 11) + ((nm >> 10) & 1ULL);  // in [2^52, 2^53]
+  const int eb = ebase - lz;                               // biased exponent
+  uint64_t bits = ((uint64_t)(int64_t)(eb - 1) << 52) + m53;
+  bits = (v == 0 || eb <= 0) ? 0ULL : bits;
+  return __longlong_as_double((long long)(bits | ((uint64_t)a & 0x8000000000000000ULL)));
+}
+
+// Apply one rotation with coset coordinates U (compile-time) to V cosets;
+// sg[v] is the sign bit (-1)^{popc(rep_v & z)}, bit l of zt the element's.
+template <int D, int V, int U, int IMAG>
+__device__ __forceinline__ void apply_fx(int64_t (&re)[V][1 << D], int64_t (&im)[V][1 << D], const int (&sg)[V],
+                                         uint32_t zt, int32_t th0, int32_t tl0, int32_t th1, int32_t tl1) {
+  const int64_t bias = int64_t(3) << 29;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+#pragma unroll
+    for (int l = 0; l < (1 << D); ++l) {
+      const int s = sg[v] ^ (int)((zt >> l) & 1u);
+      const int32_t th = s ? th1 : th0, tl = s ? tl1 : tl0;
+      if (U == 0) {
+        const int64_t r = re[v][l], i = im[v][l];
+        re[v][l] = fx_msub(r, i, th, tl, bias);
+        im[v][l] = fx_madd(i, r, th, tl, bias);
+      } else if ((l ^ U) > l) {
+        const int m = l ^ U;
+        const int64_t rl = re[v][l], il = im[v][l], rm = re[v][m], iv = im[v][m];
+        if (IMAG) {
+          re[v][l] = fx_msub(rl, iv, th, tl, bias);
+          im[v][l] = fx_madd(il, rm, th, tl, bias);
+          re[v][m] = fx_msub(rm, il, th, tl, bias);
+          im[v][m] = fx_madd(iv, rl, th, tl, bias);
+        } else {
+          re[v][l] = fx_madd(rl, rm, th, tl, bias);
+          im[v][l] = fx_madd(il, iv, th, tl, bias);
+          re[v][m] = fx_msub(rm, rl, th, tl, bias);
+          im[v][m] = fx_msub(iv, il, th, tl, bias);
+        }
+      }
+    }
+  }
+}
+
+#define PR_CASE_FX(K)                                                                      \
+  case K:                                                                                  \
+    if constexpr ((((K) >> 1) < (1 << D)) && ((((K) >> 1) != 0) || ((K)&1)))               \
+      apply_fx<D, V, ((K) >> 1), ((K)&1)>(re, im, sg, zt, th0, tl0, th1, tl1);             \
+    break;
+#define PR_CASE_FX8(B)                                                                                       \
+  PR_CASE_FX(B + 0) PR_CASE_FX(B + 1) PR_CASE_FX(B + 2) PR_CASE_FX(B + 3) PR_CASE_FX(B + 4) PR_CASE_FX(B + 5) \
+  PR_CASE_FX(B + 6) PR_CASE_FX(B + 7)
+
+template <int D, int V>
+__device__ __forceinline__ void dispatch_fx(uint32_t code, int64_t (&re)[V][1 << D], int64_t (&im)[V][1 << D],
+                                            const int (&sg)[V], uint32_t zt, int32_t th0, int32_t tl0, int32_t th1,
+                                            int32_t tl1) {
+  switch (code) {
+    PR_CASE_FX8(0)
+    PR_CASE_FX8(8)
+    PR_CASE_FX8(16)
+    PR_CASE_FX8(24)
+    PR_CASE_FX8(32)
+    PR_CASE_FX8(40)
+    PR_CASE_FX8(48)
+    PR_CASE_FX8(56)
+    default:
+      break;
+  }
+}
+
+template <typename Idx, int D>
+__host__ __device__ constexpr size_t ws_coset_fx() {
+  return ((sizeof(RotFx<Idx>) * kMaxRunRots + sizeof(Idx) * (1u << D) + 15) & ~size_t(15)) +
+         sizeof(uint32_t) * (kThreads / 32);
+}
+
+// One CTA's share of a fused complex128 run in fixed point.  The run must hold
+// at most kThreads rotations (kMaxRunRots == kThreads).  ws: ws_coset_fx bytes.
+template <typename Idx, int D, int V>
+__device__ __forceinline__ void body_coset_fx(double2 *__restrict__ amp, Idx n_cosets, const RunDev &run,
+                                              const RotDev *__restrict__ rots, uint64_t fx, uint64_t fz,
+                                              Idx cta_rank, Idx cta_count, char *ws) {
+  static_assert(kMaxRunRots <= kThreads, "one rotation record per thread");
+  constexpr int E = 1 << D;
+  RotFx<Idx> *srot = (RotFx<Idx> *)ws;
+  Idx *soff = (Idx *)(ws + sizeof(RotFx<Idx>) * kMaxRunRots);
+  uint32_t *swarp = (uint32_t *)(ws + ((sizeof(RotFx<Idx>) * kMaxRunRots + sizeof(Idx) * E + 15) & ~size_t(15)));
+  const int count = run.count;
+  const int j = threadIdx.x;
+  const int lane = j & 31, warp = j >> 5;
+
+  // records: limbs of +-T and the growth bound of each rotation,
+  // ceil(log2(1 + t^2) / 2 * 2^20) + 1 (a slight over-estimate)
+  uint32_t g = 0;
+  RotFx<Idx> rec;
+  if (j < count) {
+    const RotDev r = rots[run.first + j];
+    double t = r.t;
+    if (__popcll((r.x & fz) ^ (r.z & fx)) & 1) t = -t;  // runtime frame sign
+    long long T = __double2ll_rn(t * kTwo62);
+    T = T > kTMax ? kTMax : (T < -kTMax ? -kTMax : T);
+    fx_limbs(T, rec.th[0], rec.tl[0]);
+    fx_limbs(-T, rec.th[1], rec.tl[1]);
+    rec.z = (Idx)r.z;
+    rec.zt = r.zt;
+    rec.code = r.code & kCodeMask;
+    const float tf = (float)t;
+    g = (uint32_t)ceilf(0.5f * __log2f(1.0f + tf * tf) * (float)(1 << kGrowthFrac)) + 1u;
+  }
+  // inclusive prefix sum of g over the run (block scan)
+  uint32_t c = g;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, c, o);
+    if (lane >= o) c += y;
+  }
+  if (lane == 31) swarp[warp] = c;
+  __syncthreads();
+  uint32_t base = 0;
+  for (int w = 0; w < warp; ++w) base += swarp[w];
+  c += base;
+  if (j < count) {
+    rec.halve = (int32_t)((c >> kGrowthFrac) - ((c - g) >> kGrowthFrac));
+    srot[j] = rec;
+  }
+  if (threadIdx.x < E) {
+    uint64_t s = 0;
+    for (int b = 0; b < D; ++b)
+      if ((threadIdx.x >> b) & 1) s ^= run.basis[b];
+    soff[threadIdx.x] = (Idx)s;
+  }
+  __syncthreads();
+
+  // headroom: the coset's 2-norm is at most 2^((D+1)/2) times its largest
+  // component, and the growth between halvings stays below one bit
+  constexpr int kHead = (D + 2) / 2 + 1;
+  const Idx chunk = (Idx)blockDim.x * V;
+  const Idx stride = cta_count * chunk;
+  for (Idx c0 = cta_rank * chunk + threadIdx.x; c0 < n_cosets; c0 += stride) {
+    int64_t re[V][E], im[V][E];
+    Idx rep[V];
+    bool ok[V];
+    int S[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const Idx cc = c0 + (Idx)(v * blockDim.x);
+      Idx r = cc;
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        const int p = run.piv[b];
+        r = ((r >> p) << (p + 1)) | (r & ((Idx(1) << p) - 1));
+      }
+      rep[v] = r;
+      ok[v] = cc < n_cosets;
+      double2 a[E];
+      int emax = 0;
+#pragma unroll
+      for (int l = 0; l < E; ++l) {
+        a[l] = ok[v] ? amp[r ^ soff[l]] : make_double2(0.0, 0.0);
+        const int ex = (int)((__double_as_longlong(a[l].x) >> 52) & 0x7ff);
+        const int ey = (int)((__double_as_longlong(a[l].y) >> 52) & 0x7ff);
+        emax = max(emax, max(ex, ey));
+      }
+      // |a| < 2^(emax - 1022); S = 61 - (emax - 1022) - kHead keeps |A| < 2^61
+      S[v] = 1083 - emax - kHead;
+      const int kbase = 1085 - S[v];
+#pragma unroll
+      for (int l = 0; l < E; ++l) {
+        re[v][l] = fx_in(a[l].x, kbase);
+        im[v][l] = fx_in(a[l].y, kbase);
+      }
+    }
+    int halved = 0;
+    for (int jj = 0; jj < count; ++jj) {
+      const RotFx<Idx> s = srot[jj];
+      int sg[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) sg[v] = parity(rep[v] & s.z);
+      dispatch_fx<D, V>(s.code, re, im, sg, s.zt, s.th[0], s.tl[0], s.th[1], s.tl[1]);
+      // written as a loop (trip count 0 or 1) so that the rare halving stays a
+      // branch instead of being computed and selected after every rotation
+      for (int h = s.halve; h > 0; --h) {
+        ++halved;
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int l = 0; l < E; ++l) {
+            re[v][l] >>= 1;
+            im[v][l] >>= 1;
+          }
+      }
+    }
+    // the fold (a complex factor, last pass of a plan) in FP64 after the
+    // conversion; two separate store loops keep the FP64 multiplies out of the
+    // passes without a fold
+    if (run.fold) {
+      const double fr = run.fold_re, fi = run.fold_im;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int ebase = 1086 - (S[v] - halved);
+#pragma unroll
+        for (int l = 0; l < E; ++l) {
+          const double x = fx_out(re[v][l], ebase), y = fx_out(im[v][l], ebase);
+          if (ok[v]) amp[rep[v] ^ soff[l]] = make_double2(fr * x - fi * y, fr * y + fi * x);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int ebase = 1086 - (S[v] - halved);
+#pragma unroll
+        for (int l = 0; l < E; ++l)
+          if (ok[v]) amp[rep[v] ^ soff[l]] = make_double2(fx_out(re[v][l], ebase), fx_out(im[v][l], ebase));
+      }
+    }
+  }
+  __syncthreads();  // the workspace may be reused by the caller's next pass
+}
+
+}  // namespace
+
+}  // namespace pr

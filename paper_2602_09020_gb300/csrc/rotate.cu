@@ -26,6 +26,7 @@
 
 #include <mutex>
 
+#include "coset_fx.cuh"
 #include "kernels.cuh"
 
 namespace pr {
@@ -38,6 +39,15 @@ __global__ void __launch_bounds__(kThreads)
             const RotDev *__restrict__ rots, uint64_t fx, uint64_t fz) {
   __shared__ __align__(16) char ws[ws_coset<R, Idx, D>()];
   body_coset<R, Idx, D, V>(amp, n_cosets, run, rots, fx, fz, (Idx)blockIdx.x, (Idx)gridDim.x, ws);
+}
+
+// complex128 runs in 64-bit fixed point on the integer pipes (coset_fx.cuh)
+template <typename Idx, int D, int V>
+__global__ void __launch_bounds__(kThreads)
+    k_coset_fx(double2 *__restrict__ amp, Idx n_cosets, const __grid_constant__ RunDev run,
+               const RotDev *__restrict__ rots, uint64_t fx, uint64_t fz) {
+  __shared__ __align__(16) char ws[ws_coset_fx<Idx, D>()];
+  body_coset_fx<Idx, D, V>(amp, n_cosets, run, rots, fx, fz, (Idx)blockIdx.x, (Idx)gridDim.x, ws);
 }
 
 template <typename Idx, int D>
@@ -83,6 +93,35 @@ int launch_coset_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_
   trace_end(sv, tr, KN_COSET0 + D, 2.0 * (double)sizeof(C) * (double)(1ULL << sv->n),
             4.0 * (double)run.count * (double)(1ULL << sv->n));
   return SV_OK;
+}
+
+template <typename Idx, int D, int V>
+int launch_coset_fx_t(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t fx, uint64_t fz) {
+  static const int cap = occupancy_blocks(k_coset_fx<Idx, D, V>, kThreads);
+  const uint64_t n_cosets = (1ULL << sv->n) >> D;
+  uint64_t need = (n_cosets + (uint64_t)kThreads * V - 1) / ((uint64_t)kThreads * V);
+  unsigned blocks = (unsigned)(need < (uint64_t)cap ? need : (uint64_t)cap);
+  if (!blocks) blocks = 1;
+  const int tr = trace_begin(sv, KN_COSET0 + D);
+  k_coset_fx<Idx, D, V><<<blocks, kThreads, 0, sv->stream>>>((double2 *)sv->amps, (Idx)n_cosets, run,
+                                                             plan->d_rots, fx, fz);
+  PR_CHECK_LAUNCH();
+  trace_end(sv, tr, KN_COSET0 + D, 2.0 * 16.0 * (double)(1ULL << sv->n),
+            4.0 * (double)run.count * (double)(1ULL << sv->n));
+  return SV_OK;
+}
+
+template <typename Idx>
+int launch_coset_fx_d(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t fx, uint64_t fz) {
+  switch (run.d) {
+    case 0: return launch_coset_fx_t<Idx, 0, 2>(sv, plan, run, fx, fz);
+    case 1: return launch_coset_fx_t<Idx, 1, 1>(sv, plan, run, fx, fz);
+    case 2: return launch_coset_fx_t<Idx, 2, 1>(sv, plan, run, fx, fz);
+    case 3: return launch_coset_fx_t<Idx, 3, 1>(sv, plan, run, fx, fz);
+    case 4: return launch_coset_fx_t<Idx, 4, 1>(sv, plan, run, fx, fz);
+    case 5: return launch_coset_fx_t<Idx, 5, 1>(sv, plan, run, fx, fz);
+    default: return fail(SV_EINVAL, "run dimension %d out of range", run.d);
+  }
 }
 
 template <typename Idx, int D>
@@ -255,8 +294,8 @@ int launch_run(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t fx
   if (use_c64x2(sv, run))
     return narrow ? launch_c64x2_d<uint32_t>(sv, plan, run, fx, fz) : launch_c64x2_d<uint64_t>(sv, plan, run, fx, fz);
   if (sv->dtype == SV_C128)
-    return narrow ? launch_coset_d<double, uint32_t>(sv, plan, run, fx, fz)
-                  : launch_coset_d<double, uint64_t>(sv, plan, run, fx, fz);
+    return narrow ? launch_coset_fx_d<uint32_t>(sv, plan, run, fx, fz)
+                  : launch_coset_fx_d<uint64_t>(sv, plan, run, fx, fz);
   return narrow ? launch_coset_d<float, uint32_t>(sv, plan, run, fx, fz)
                 : launch_coset_d<float, uint64_t>(sv, plan, run, fx, fz);
 }

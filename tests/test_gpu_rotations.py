@@ -284,3 +284,52 @@ def test_invalid_inputs_fail_without_side_effects():
     with pytest.raises(capi.PauliRotError) as e:
         capi.sv_alloc(40, "c128")
     assert e.value.code == capi.SV_ENOMEM
+
+
+@pytest.mark.parametrize("scale_exp", [-700, -300, 0, 300, 700])
+def test_c128_block_exponent_follows_the_state_scale(orc, scale_exp):
+    """The complex128 pass computes in fixed point with one exponent per coset
+    chosen from the coset's largest component: a state scaled by 2^k (k up to
+    +-700, far outside any fixed grid) must give the scaled result with the
+    same relative accuracy, for fused runs of every depth."""
+    n = 10
+    psi0 = synth.random_state(n, 77)
+    s = 2.0 ** scale_exp
+    for depth in (1, 3, 5):
+        x, z = random_paulis(n, 90, seed=5 + depth, span_dim=depth, diag_frac=0.1)
+        th = np.random.default_rng(depth).uniform(-np.pi, np.pi, size=90)
+        want = run_oracle(orc, n, psi0, x, z, th)
+        got, _ = run_gpu(n, "c128", psi0 * s, x, z, th, depth)
+        assert_close_c128(want, got / s, what=f"scale 2^{scale_exp} depth {depth}")
+
+
+def test_c128_long_runs_of_large_angles(orc):
+    """Runs of up to 256 rotations at angles near +-pi/2 grow the tan-form norm
+    by up to half a bit per rotation (about 128 bits per run): the fixed-point
+    pass halves its components as the growth passes each whole bit, and the
+    running scale folds the cos factors back in."""
+    n = 9
+    psi0 = synth.random_state(n, 3)
+    g = np.random.default_rng(11)
+    for span in (1, 2, 3):
+        x, z = random_paulis(n, 256, seed=20 + span, span_dim=span)
+        th = np.where(g.random(256) < 0.5, -1.0, 1.0) * g.uniform(1.45, np.pi / 2, size=256)
+        want = run_oracle(orc, n, psi0, x, z, th)
+        got, (nrot, nruns, _) = run_gpu(n, "c128", psi0, x, z, th, span)
+        assert nruns <= 4, nruns  # long runs really are fused
+        assert_close_c128(want, got, what=f"large angles, span {span}")
+
+
+def test_c128_tiny_components_beside_large_ones(orc):
+    """A coset holding components of very different size: the fixed point is
+    set by the largest, so values below 2^-57 of it may be dropped, within the
+    complex128 tolerance of 1e-12 absolute (the state is normalised)."""
+    n = 8
+    psi0 = synth.random_state(n, 5)
+    psi0[::2] *= 1e-30  # every even amplitude tiny, odd ones of normal size
+    psi0 /= np.linalg.norm(psi0)
+    x, z = random_paulis(n, 60, seed=9, span_dim=3)
+    th = np.random.default_rng(9).uniform(-np.pi, np.pi, size=60)
+    want = run_oracle(orc, n, psi0, x, z, th)
+    got, _ = run_gpu(n, "c128", psi0, x, z, th, 3)
+    assert_close_c128(want, got, what="tiny beside large")
