@@ -163,14 +163,20 @@ int frame_get(sv_state *sv, uint64_t *xq, uint64_t *zq, int *phase);
 /* ---- rotations ----------------------------------------------------------------- */
 
 /* Apply R_{P_0}(angles[0]) first, then P_1, ... to the represented state.
- * Host arrays of length count.  Each rotation is rewritten by the frame
+ * R_P(theta) = exp(-i theta/2 P) = cos(theta/2) I - i sin(theta/2) P, applied
+ * as the pair update of amplitudes k and k XOR x (paper, Sec. "Multi-qubit
+ * rotations in a fullstate simulator" and App. "Amplitude update rule for
+ * multi-qubit rotations").  Host arrays of length count.  Each rotation is rewritten by the frame
  * (sign flip where P anticommutes with Q), the list is compiled into fused
  * runs (same work as plan_create with fusion_depth = -1) and launched on the
  * handle's stream.  Returns before the device work finishes. */
 int apply_pauli_rotations(sv_state *sv, const uint64_t *x, const uint64_t *z,
                           const double *angles, size_t count);
 
-/* Compile a rotation list once for states of n qubits and this dtype.
+/* Compile a rotation list once for states of n qubits and this dtype: the
+ * rotations of Sec. "Multi-qubit rotations in a fullstate simulator", in list
+ * order, grouped into fused runs (one pass over the amplitudes per run; the
+ * grouping is this library's, the paper applies one rotation per pass).
  * fusion_depth = maximum dimension of the span of x-masks fused into one
  * pass (0..5; -1 = the depth plan_tuned_depth reports: the autotuned one for
  * (n, dtype) if one is recorded, else 3 for complex128 and 4 for complex64).  The plan's device buffers
@@ -179,7 +185,9 @@ int apply_pauli_rotations(sv_state *sv, const uint64_t *x, const uint64_t *z,
 int plan_create(sv_plan **out, int n_qubits, int dtype, const uint64_t *x, const uint64_t *z,
                 const double *angles, size_t count, int fusion_depth, void *cuda_stream);
 
-/* Apply a plan to a state (same n and dtype).  The frame signs are taken from
+/* Apply a plan to a state (same n and dtype): its rotations in list order, as
+ * apply_pauli_rotations would (Sec. "Multi-qubit rotations in a fullstate
+ * simulator").  The frame signs are taken from
  * the handle's frame at call time (a captured graph replays the frame it was
  * captured with).  Updates the handle's frame on the host. */
 int plan_apply(sv_state *sv, sv_plan *plan);
@@ -277,7 +285,9 @@ int trotter_expand(const uint64_t *x, const uint64_t *z, const double *c, size_t
 
 /* ---- reductions (FP64) ----------------------------------------------------------- */
 
-/* out_energy = <psi|sum_j c_j P_j|psi> for the represented state, FP64.
+/* out_energy = <psi|sum_j c_j P_j|psi> for the represented state, FP64, as
+ * sum_j c_j <phi|Q^dag P_j Q|phi> with the Pauli frame Q (paper, Sec.
+ * "Extraction of Expectation Values", Eqs. Fmap and chfsexp).
  * out_norm2 (nullable) = <psi|psi>.  Terms are grouped by x-mask and several
  * groups are evaluated per pass; partial sums are reduced in a fixed order,
  * so repeated calls give bitwise-equal results. */
@@ -307,7 +317,10 @@ int expval_pauli_sum_noalloc(sv_state *sv, const uint64_t *x, const uint64_t *z,
                              size_t count, double *out_energy, double *out_norm2);
 
 /* dst <- sum_j c_j P_j applied to src's represented state (dst gets the
- * identity frame).  Same n and dtype; dst must not be src. */
+ * identity frame): each P_j maps amplitude k to k XOR x_j with the phase
+ * i^{nY} (-1)^{popc(k & z_j)} (Sec. "Multi-qubit rotations in a fullstate
+ * simulator"); the sum is the seed H psi of the adjoint gradient (not in the
+ * paper).  Same n and dtype; dst must not be src. */
 int apply_pauli_sum(sv_state *dst, sv_state *src, const uint64_t *x, const uint64_t *z,
                     const double *coeff, size_t count);
 
@@ -414,6 +427,19 @@ int sv_trace_start_ex(sv_state *sv, int mode);
 /* Stop recording, synchronise the stream and aggregate per kernel name into
  * rows (at most cap; *n_rows = rows written).  Events are recycled. */
 int sv_trace_stop(sv_state *sv, sv_trace_row *rows, int cap, int *n_rows);
+
+/* ---- arithmetic-rate probe (not in the paper) ----------------------------------------- */
+
+/* Launch one probe kernel on cuda_stream (no synchronisation) that keeps one
+ * arithmetic pipe busy: `blocks` CTAs of 256 threads, each thread running eight
+ * independent dependency chains of `iters` operations.  kind 0: FP64 fused
+ * multiply-add; kind 1: 32 x 32 -> 64-bit signed integer multiply-add (the
+ * operation the complex128 passes are built from).  The caller times the launch
+ * with CUDA events; *out_ops (nullable) = operations the launch performs
+ * (blocks * 256 * iters * 8).  dev_out: caller-owned device buffer of
+ * blocks * 256 eight-byte values, overwritten with the chains' results.
+ * SV_EINVAL for another kind, blocks < 1, iters < 1 or a null buffer. */
+int sv_probe_rate(int kind, int blocks, int iters, void *dev_out, void *cuda_stream, double *out_ops);
 
 /* ---- Clifford-fullstate hybrid: general Clifford frames ------------------------------------ *
  *
@@ -524,6 +550,59 @@ int cfhs_measure_pauli(sv_state *sv, const sv_cliff *f, uint64_t x, uint64_t z, 
  * anticommuting partner (Z for X and Y, X for Z) through the frames, so that
  * no extra pass runs.  *out_outcome (nullable) = the measured outcome. */
 int cfhs_prepare_qubit(sv_state *sv, const sv_cliff *f, int qubit, char pauli, double u, int *out_outcome);
+
+/* ---- global-qubit sharding (host planning) ---------------------------------------------- *
+ *
+ * Paper, Sec. "Multi-qubit rotations in a fullstate simulator", distributed-
+ * memory paragraph: the amplitudes of n qubits are split over 2^g ranks by their
+ * top g index bits (the global qubits); rank r holds the slice of L = n - g local
+ * qubits whose top bits are r.  A rotation whose x-mask has no global bit acts
+ * inside every slice; one whose global x-part is X pairs rank r with rank r ^ X,
+ * and the two exchange slices.  A rank places the slice it receives beside its
+ * own: the two form a state of L + 1 qubits (bit L = 0 for its own slice, 1 for
+ * the partner's), its "pair state", on which the rotations of that exchange act
+ * as ordinary rotations.  These calls rewrite rotations and terms for one rank;
+ * they do no device work and need no GPU (the exchange and the passes are the
+ * caller's: see paper_2602_09020_gb300/shard.py). */
+typedef struct sv_shard_step {
+  int32_t kind;    /* 0: on the rank's own slice (L qubits); 1: on its pair state (L + 1 qubits) */
+  int32_t partner; /* kind 1: the rank whose slice is exchanged (rank ^ X); kind 0: the rank */
+  int64_t first;   /* entries [first, first + count) of the rewritten arrays */
+  int64_t count;
+} sv_shard_step;
+
+/* Rewrite the rotation list (x, z, theta; count entries, masks on n_qubits) for
+ * `rank` of 2^global_qubits ranks.  With a Clifford frame F (nullable; on
+ * n_qubits, see the cliff_* calls below) each rotation about P is first taken
+ * about F(P) with its sign folded into theta, as cfhs_apply_rotations does.  The list is cut, in order, into steps: a step
+ * of kind 0 holds rotations with no global x-bit; a step of kind 1 holds the
+ * rotations from one with global x-part X to the last one with that X before a
+ * rotation with another non-zero global x-part (rotations with no global x-bit in
+ * between stay in it).  The cut depends only on the masks, so every rank gets the
+ * same steps.  Rotation j is written to out_x[j], out_z[j], out_theta[j] (arrays of
+ * count) in its step's frame: local masks and theta (-1)^{popc(r & z_g)} for kind
+ * 0; pair masks (bit L set in x when the rotation crosses, in z when
+ * popc(X & z_g) is odd) and theta times the pair sign for kind 1 (derivation in
+ * csrc/shard.cu).  At most step_cap steps are written; *out_steps = steps needed
+ * (SV_EINVAL if above step_cap).  SV_EINVAL for masks with bits >= n_qubits,
+ * global_qubits outside 0..n-1 or rank outside 0..2^g - 1. */
+int shard_rotations(int n_qubits, int global_qubits, int rank, const sv_cliff *frame, const uint64_t *x,
+                    const uint64_t *z, const double *theta, size_t count, sv_shard_step *steps, size_t step_cap,
+                    size_t *out_steps, uint64_t *out_x, uint64_t *out_z, double *out_theta);
+
+/* Rewrite the Pauli sum sum_j c_j P_j for `rank` (terms mapped through the
+ * nullable frame F first, as cfhs_expval does): group 0 (kind 0, always first,
+ * possibly empty) holds the terms with no global x-bit, as local strings with
+ * coefficient c_j (-1)^{popc(r & z_g)}; then one group (kind 1) per distinct
+ * non-zero global x-part X, in order of first appearance, as pair strings with
+ * coefficient c_j sigma / 2 (each of the two ranks of a pair evaluates the term
+ * over the same pair state).  The sum over all ranks of <own|group 0|own> plus
+ * <pair|group k|pair> for every group k is <psi|H|psi>.  Terms are written group
+ * by group to out_x/out_z/out_coeff (arrays of count); at most group_cap groups;
+ * *out_groups = groups needed. */
+int shard_terms(int n_qubits, int global_qubits, int rank, const sv_cliff *frame, const uint64_t *x,
+                const uint64_t *z, const double *coeff, size_t count, sv_shard_step *groups, size_t group_cap,
+                size_t *out_groups, uint64_t *out_x, uint64_t *out_z, double *out_coeff);
 
 #ifdef __cplusplus
 }

@@ -101,6 +101,9 @@ def lib() -> ctypes.CDLL:
         "sv_trace_start": ([vp], i),
         "sv_trace_start_ex": ([vp, i], i),
         "sv_trace_stop": ([vp, vp, i, P(i)], i),
+        "sv_probe_rate": ([i, i, i, vp, vp, P(d)], i),
+        "shard_rotations": ([i, i, i, vp, vp, vp, vp, sz, vp, sz, P(sz), vp, vp, vp], i),
+        "shard_terms": ([i, i, i, vp, vp, vp, vp, sz, vp, sz, P(sz), vp, vp, vp], i),
         "cliff_create": ([P(vp), i], i),
         "cliff_free": ([vp], i),
         "cliff_reset": ([vp], i),
@@ -136,7 +139,8 @@ def exported_symbols() -> Sequence[str]:
             "apply_pauli_rotations_gates", "batch_run", "batch_run_ex", "batch_info", "batch_inspect", "sv_trace_start",
             "sv_trace_start_ex", "sv_trace_stop", "cliff_create", "cliff_free", "cliff_reset", "cliff_num_qubits", "cliff_apply_gates",
             "cliff_map_paulis", "cliff_entry", "cliff_is_origin", "cliff_inverse_rotations", "cfhs_apply_gates",
-            "cfhs_apply_rotations", "cfhs_expval", "cfhs_materialize", "cfhs_measure_pauli", "cfhs_prepare_qubit"]
+            "cfhs_apply_rotations", "cfhs_expval", "cfhs_materialize", "cfhs_measure_pauli", "cfhs_prepare_qubit",
+            "sv_probe_rate", "shard_rotations", "shard_terms"]
 
 
 def _check(rc: int) -> None:
@@ -478,6 +482,51 @@ def sv_trace_stop(sv: int) -> dict:
     _check(lib().sv_trace_stop(sv, rows, 64, ctypes.byref(n)))
     return {rows[i].name.decode(): (int(rows[i].launches), float(rows[i].total_ms), float(rows[i].bytes),
                                     float(rows[i].flops)) for i in range(n.value)}
+
+
+def sv_probe_rate(kind: int, blocks: int, iters: int, dev_out: int, stream: int = 0) -> float:
+    """Launch one arithmetic-rate probe (kind 0: FP64 FMA, 1: 32x32->64 integer
+    multiply-add) on `stream`; returns the operations it performs."""
+    ops = ctypes.c_double()
+    _check(lib().sv_probe_rate(int(kind), int(blocks), int(iters), ctypes.c_void_p(dev_out),
+                               ctypes.c_void_p(stream), ctypes.byref(ops)))
+    return ops.value
+
+
+# ------------------------------------------------------------------ global-qubit sharding (host)
+
+class ShardStep(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("partner", ctypes.c_int32), ("first", ctypes.c_int64),
+                ("count", ctypes.c_int64)]
+
+
+def _shard_call(name, n_qubits, global_qubits, rank, frame, x, z, v):
+    x, z, v = _u64(x), _u64(z), _f64(v)
+    if not (len(x) == len(z) == len(v)):
+        raise ValueError("x, z and the values must have equal length")
+    cap = len(v) + 1
+    steps = (ShardStep * cap)()
+    ns = ctypes.c_size_t()
+    ox, oz, ov = np.zeros(len(v), np.uint64), np.zeros(len(v), np.uint64), np.zeros(len(v), np.float64)
+    _check(getattr(lib(), name)(int(n_qubits), int(global_qubits), int(rank), frame, _p(x), _p(z), _p(v),
+                                len(v), steps, cap, ctypes.byref(ns), _p(ox), _p(oz), _p(ov)))
+    out = [(int(steps[k].kind), int(steps[k].partner), int(steps[k].first), int(steps[k].count))
+           for k in range(ns.value)]
+    return out, ox, oz, ov
+
+
+def shard_rotations(n_qubits: int, global_qubits: int, rank: int, x, z, theta, frame: Optional[int] = None):
+    """Rotations rewritten for one rank of a sharded state (through the Clifford
+    frame `frame` first, if given): returns (steps, x, z, theta) with steps =
+    [(kind, partner, first, count)]; kind 0 acts on the rank's slice, kind 1 on
+    its pair state with `partner`."""
+    return _shard_call("shard_rotations", n_qubits, global_qubits, rank, frame, x, z, theta)
+
+
+def shard_terms(n_qubits: int, global_qubits: int, rank: int, x, z, coeff, frame: Optional[int] = None):
+    """Pauli terms rewritten for one rank: returns (groups, x, z, coeff) with
+    groups = [(kind, partner, first, count)], group 0 local to the slice."""
+    return _shard_call("shard_terms", n_qubits, global_qubits, rank, frame, x, z, coeff)
 
 
 # ------------------------------------------------------------------ Clifford-fullstate hybrid
