@@ -41,8 +41,6 @@ sys.path.insert(0, ROOT)
 from paper_2602_09020_gb300 import synth  # noqa: E402
 
 METRIC = "Pauli rotations/s at n=24 & HBM fraction; speedup vs gate-decomposed, same GPU"
-# GB300 FP64: 1.25 TFLOP/s nominal (2 FMA per SM per clock, 152 SMs, ~2.07 GHz)
-FP64_PEAK_TFLOPS = 1.25
 
 
 def parse_args():
@@ -175,17 +173,36 @@ class Clocks:
 
 # ------------------------------------------------------------------ CPU oracle
 
-def oracle_rate(n, rx, rz, rt, seconds: float, basis: int):
-    """Apply rotations with the oracle until `seconds` pass; returns (rot/s, count, threads, s)."""
+def strided_sample(rx, rz, rt, count: int, period: int):
+    """Every k-th rotation of the first `period` rotations (one Trotter step: the
+    list repeats it), k chosen so that about `count` are taken.  The oracle's
+    cost per rotation depends only on the string's support, so a stride across
+    a whole step gives the list's mix of localities, which a prefix does not
+    (the step starts with all its Z and ZZ terms)."""
+    period = min(period, len(rt))
+    k = max(1, period // max(1, count))
+    sel = np.arange(0, period, k)
+    return rx[sel], rz[sel], rt[sel], k
+
+
+def oracle_rate(n, rx, rz, rt, seconds: float, basis: int, period: int):
+    """Time the oracle on a strided sample of one Trotter step sized to take
+    about `seconds`: a short pilot (every 50th rotation of the step) gives the
+    rate, then the sample is drawn at the stride that fills the time.
+    Returns (rot/s, count, threads, elapsed s, stride, mean locality of the sample)."""
     import oracle
+    px, pz, pt, _ = strided_sample(rx, rz, rt, max(2, period // 50), period)
     psi = oracle.basis_state(n, basis)
     t0 = time.perf_counter()
-    k = 0
-    while k < len(rt) and (k < 2 or time.perf_counter() - t0 < seconds):
-        oracle.apply_rotation(psi, n, int(rx[k]), int(rz[k]), float(rt[k]))
-        k += 1
+    oracle.apply_rotations(psi, n, px[:8], pz[:8], pt[:8])
+    pilot = 8 / (time.perf_counter() - t0)
+    sx, sz, st, stride = strided_sample(rx, rz, rt, max(2, int(pilot * seconds)), period)
+    psi = oracle.basis_state(n, basis)
+    t0 = time.perf_counter()
+    oracle.apply_rotations(psi, n, sx, sz, st)
     el = time.perf_counter() - t0
-    return k / el, k, oracle.num_threads(), el
+    loc = float(synth.locality(sx, sz).mean())
+    return len(st) / el, len(st), oracle.num_threads(), el, stride, loc
 
 
 def run_reference(a):
@@ -196,21 +213,25 @@ def run_reference(a):
     ham = synth.jw_hamiltonian(a.n, a.terms, a.seed)
     rx, rz, rt = oracle.trotter_rotations(ham.x, ham.z, ham.c, a.dt, a.trotter_steps, 1)
     basis = synth.hartree_fock_index(a.n // 2)
-    # calibrate a sample so that warmup + steps take about two minutes
-    r1, _, threads, _ = oracle_rate(a.n, rx, rz, rt, 2.0, basis)
-    per_step = max(2, int(r1 * 120.0 / max(1, a.steps + a.warmup)))
-    per_step = min(per_step, len(rt))
+    # a strided sample of one Trotter step, sized so that warmup + steps take
+    # about two minutes (the oracle's cost per rotation depends only on the
+    # string's support, so the stride keeps the list's mix of localities)
+    r1, _, threads, _, _, _ = oracle_rate(a.n, rx, rz, rt, 2.0, basis, a.terms)
+    sx, sz, st, stride = strided_sample(rx, rz, rt, max(2, int(r1 * 120.0 / max(1, a.steps + a.warmup))),
+                                        a.terms)
     times = []
     for s in range(a.warmup + a.steps):
         t0 = time.perf_counter()
         psi = oracle.basis_state(a.n, basis)
-        oracle.apply_rotations(psi, a.n, rx[:per_step], rz[:per_step], rt[:per_step])
+        oracle.apply_rotations(psi, a.n, sx, sz, st)
         el = time.perf_counter() - t0
         if s >= a.warmup:
             times.append(el)
     ms = 1000.0 * statistics.mean(times)
-    value = per_step / (ms / 1000.0)
-    sample = f"first {per_step} of {len(rt)} rotations per step (n={a.n}, complex128, gate-decomposed)"
+    value = len(st) / (ms / 1000.0)
+    sample = (f"every {stride}th rotation of the first Trotter step ({len(st)} of {len(rt)} rotations per step, "
+              f"mean locality {float(synth.locality(sx, sz).mean()):.2f} vs "
+              f"{float(synth.locality(rx, rz).mean()):.2f} for the list; n={a.n}, complex128, gate-decomposed)")
     line = {"metric": METRIC, "value": value, "unit": "rotations/s", "impl": "reference", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
@@ -310,18 +331,30 @@ def run_ours(a):
                   "ms_per_launch": tot_ms / launches, "algorithmic_bytes_per_launch": by / launches,
                   "algorithmic_flops_per_launch": fl / launches,
                   "hbm_gbs": by / (tot_ms / 1000.0) / 1e9}
+        achieved = by / (tot_ms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "peak_source": pk["source"]}
         if dtype == "c128" and name.startswith("k_coset"):
-            # the complex128 pass is bound by the FP64 pipe (2 FMA per SM per clock on
-            # GB300, 1.25 TFLOP/s nominal); bytes are reported beside it
-            achieved = fl / (tot_ms / 1000.0) / 1e12
-            roof = {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "nominal"}
-        else:
-            achieved = by / (tot_ms / 1000.0) / 1e9
-            roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / pk["hbm_gbs"], "peak_source": pk["source"]}
+            # the complex128 pass runs its products on the integer pipes: per
+            # amplitude and rotation two 62-bit fixed-point products of three
+            # 32x32->64 multiply-adds each (the trace counts 4 FP64-equivalent
+            # flops there); the wide-multiply rate is set against the measured
+            # peak of the probe kernel when the bench has measured it
+            imads = 1.5 * fl / (tot_ms / 1000.0) / 1e12
+            roof["alu"] = {"pipe": "int_mul_wide", "achieved": imads, "unit": "Tops/s",
+                           "ops_per_amplitude_rotation": 6,
+                           "peak": int_peak.get("tops"), "peak_source": int_peak.get("source"),
+                           "frac": (imads / int_peak["tops"]) if int_peak.get("tops") else None}
         roof.update(common)
         return roof, sum(r[0] for r in rows.values())
+
+    # measured arithmetic peaks (FP64 FMA, wide integer multiply-add), taken
+    # before the timed steps so the complex128 roofline can use them
+    int_peak = {}
+    arith = None
+    if not a.skip_extras:
+        arith = probe_peaks(capi, torch)
+        int_peak = {"tops": arith["int_mul_wide_tops"], "source": "measured (probe kernel, this run)"}
 
     # the fusion depth plan_create(-1) takes comes from the library's autotuner,
     # run on the first Trotter step of the list for each precision (untimed
@@ -393,7 +426,11 @@ def run_ours(a):
         extras["cfhs_gate_stream"] = cfhs_measure(capi, torch, a.n, a.dtype, rx[:a.terms], rz[:a.terms],
                                                   rt[:a.terms], ham, basis, barrier)
         extras["large_state"] = large_measure(capi, torch, barrier)
+        extras["large_state"]["n29_c64_vs_c128"] = large_compare(capi, torch, barrier)
         extras["adjoint"] = adjoint_measure(capi, torch, barrier)
+        extras["arith_peaks"] = arith
+        extras["sharded_one_gpu"] = shard_measure(capi, torch, barrier)
+        extras["precision"] = precision_report(capi, a, ham, rx, rz, rt, basis, sh)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -431,17 +468,20 @@ def run_ours(a):
 
     cpu = None
     if world == 1 and not a.skip_extras:
-        rate, k, threads, el = oracle_rate(a.n, rx, rz, rt, 12.0, basis)
+        rate, k, threads, el, stride, loc = oracle_rate(a.n, rx, rz, rt, 12.0, basis, a.terms)
         cpu = {"value": rate, "unit": "rotations/s", "cores": threads, "kind": "oracle",
-               "sample": f"first {k} rotations of the step at n={a.n}, complex128 gate-decomposed ({el:.1f} s)"}
+               "sample": (f"every {stride}th rotation of the first Trotter step ({k} rotations, mean locality "
+                          f"{loc:.2f} vs {float(synth.locality(rx, rz).mean()):.2f} for the whole list) at "
+                          f"n={a.n}, complex128 gate-decomposed ({el:.1f} s)")}
         import oracle
         oracle.set_num_threads(1)
         try:
-            rate1, k1, _, el1 = oracle_rate(a.n, rx, rz, rt, 4.0, basis)
+            rate1, k1, _, el1, stride1, _ = oracle_rate(a.n, rx, rz, rt, 4.0, basis, a.terms)
         finally:
             oracle.set_num_threads(0)
         cpu["single_thread"] = {"value": rate1, "unit": "rotations/s", "cores": 1,
-                                "sample": f"first {k1} rotations, one thread ({el1:.1f} s)"}
+                                "sample": f"every {stride1}th rotation of the first step ({k1}), one thread "
+                                          f"({el1:.1f} s)"}
 
     if rank != 0:
         return 0
@@ -470,10 +510,187 @@ def run_ours(a):
                     for k, v in per_launch["trace"].items()},
     }
     line.update(extras)
+    prec = extras.get("precision")
+    if prec:
+        # the per-result errors against the FP64 oracle, for the headline precision
+        # and for complex128
+        line["infidelity_vs_oracle"] = prec[a.dtype]["infidelity_vs_oracle_sampled"]
+        line["energy_error_vs_oracle"] = prec[a.dtype]["energy_error_vs_oracle"]
+        line["max_abs_vs_oracle"] = prec[a.dtype]["max_abs_vs_oracle"]
+        line["c128_max_abs_vs_oracle"] = prec["c128"]["max_abs_vs_oracle"]
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden", "full_n24_trotter.npz")
+
+
+def precision_report(capi, a, ham, rx, rz, rt, basis, sh):
+    """Both precisions against the oracle's values for this workload (stored by
+    tests/golden/make_full_size.py: the FP64 gate-level oracle's amplitudes at
+    8192 seeded non-zero indices plus the largest ones, its norm and <H>).
+    Complex64: infidelity of the stored sub-vector, largest amplitude error,
+    energy error; complex128: largest amplitude error and energy error.  The
+    oracle's <H> is divided by its norm (its Hadamard passes drift the norm by a
+    uniform factor of ~1 + 2.6e-11)."""
+    if not os.path.exists(GOLDEN):
+        return None
+    g = np.load(GOLDEN)
+    if (int(g["n"]), int(g["terms"]), int(g["seed"]), float(g["dt"]), int(g["steps"])) != \
+            (a.n, a.terms, a.seed, a.dt, a.trotter_steps):
+        return None
+    idx, want = g["indices"], g["amps"]
+    e_orc = float(g["energy"]) / float(g["norm2"])
+    out = {"reference": f"FP64 gate-level oracle, {len(idx)} stored amplitudes of the final state "
+                        f"(8192 seeded draws among its {int(g['nonzero_count'])} non-zero ones, the 16 largest "
+                        f"and the initial basis state), its <H> / norm",
+           "oracle_energy": e_orc}
+    for dtype in ("c64", "c128"):
+        plan = capi.plan_create(a.n, dtype, rx, rz, rt, a.fusion_depth, sh)
+        sv = capi.sv_alloc(a.n, dtype, sh)
+        try:
+            capi.sv_set_basis_state(sv, basis)
+            capi.plan_apply(sv, plan)
+            e, nrm = capi.expval_pauli_sum(sv, ham.x, ham.z, ham.c)
+            got = capi.sv_to_host(sv, True)[idx].astype(np.complex128)
+        finally:
+            capi.sv_free(sv)
+            capi.plan_free(plan)
+        ov = np.vdot(want, got)
+        inf = float(1.0 - abs(ov) ** 2 / (np.vdot(want, want).real * np.vdot(got, got).real))
+        out[dtype] = {"max_abs_vs_oracle": float(np.max(np.abs(got - want))),
+                      "infidelity_vs_oracle_sampled": inf, "energy": e,
+                      "energy_error_vs_oracle": abs(e - e_orc), "norm2_minus_1": nrm - 1.0}
+    return out
+
+
+def probe_peaks(capi, torch, reps: int = 3) -> dict:
+    """Measured arithmetic peaks on this GPU: FP64 FMA and 32x32->64 integer
+    multiply-add rates from the library's probe kernels (grids of 8 CTAs per SM,
+    CUDA events on the launching stream, best of `reps` launches), with the SM
+    clock sampled during the launches; ops x 2 for FLOP/s."""
+    own = torch.cuda.Stream()
+    sh = int(own.cuda_stream)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks = 8 * sms
+    buf = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    out = {"blocks": blocks, "threads_per_block": 256, "chains_per_thread": 8}
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    for kind, name, iters in ((0, "fp64_fma", 4000), (1, "int_mul_wide", 40000)):
+        capi.sv_probe_rate(kind, blocks, 16, buf.data_ptr(), sh)  # warm
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(own)
+            ops = capi.sv_probe_rate(kind, blocks, iters, buf.data_ptr(), sh)
+            e1.record(own)
+            own.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out[name] = {"ops_per_s": ops / (best / 1000.0), "ms": best, "ops": ops}
+    out["fp64_tflops"] = 2.0 * out["fp64_fma"]["ops_per_s"] / 1e12
+    out["int_mul_wide_tops"] = out["int_mul_wide"]["ops_per_s"] / 1e12
+    out["clocks"] = clocks.stop()
+    return out
+
+
+def large_compare(capi, torch, barrier, n: int = 29, terms: int = 5000, seed: int = 1):
+    """n = 29 in both precisions (8 GiB and 4 GiB): one symmetric second-order
+    Trotter step of the 5000-term JW-shaped Hamiltonian (9,999 merged rotations)
+    from the Hartree-Fock state, <H> after it; complex64 against the complex128
+    GPU run: infidelity of the whole state and |dE|.  Device time per step."""
+    ham = synth.jw_hamiltonian(n, terms, seed)
+    rx, rz, rt = capi.trotter_expand(ham.x, ham.z, ham.c, 0.05, 1, 2, True)
+    own = torch.cuda.Stream()
+    sh = int(own.cuda_stream)
+    basis = synth.hartree_fock_index(n // 2)
+    res = {}
+    for dtype in ("c128", "c64"):
+        t = torch.zeros(1 << n, dtype=torch.complex128 if dtype == "c128" else torch.complex64, device="cuda")
+        sv = capi.sv_wrap(t.data_ptr(), n, dtype, sh)
+        plan = capi.plan_create(n, dtype, rx, rz, rt, -1, sh)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        try:
+            capi.sv_set_basis_state(sv, basis)
+            barrier()
+            e0.record(own)
+            capi.plan_apply(sv, plan)
+            e1.record(own)
+            e, nrm = capi.expval_pauli_sum(sv, ham.x, ham.z, ham.c)
+            capi.sv_materialize(sv)
+            barrier()
+            passes = capi.plan_stats(plan)[1]
+        finally:
+            capi.plan_free(plan)
+            capi.sv_free(sv)
+        ms = e0.elapsed_time(e1)
+        res[dtype] = (t, e, nrm, ms, passes)
+    t128, e128, n128, ms128, p128 = res["c128"]
+    t64, e64, n64, ms64, p64 = res["c64"]
+    g = t64.to(torch.complex128)
+    ov = torch.vdot(t128, g)
+    inf = float(1.0 - (ov.abs() ** 2) / (torch.vdot(t128, t128).real * torch.vdot(g, g).real))
+    del g, t64, t128
+    torch.cuda.empty_cache()
+    return {"n": n, "terms": terms, "rotations": len(rt),
+            "c128": {"rotations_ms": ms128, "passes": p128, "rotations_per_s": len(rt) / (ms128 / 1000.0),
+                     "energy": e128, "norm_drift": abs(n128 - 1.0)},
+            "c64": {"rotations_ms": ms64, "passes": p64, "rotations_per_s": len(rt) / (ms64 / 1000.0),
+                    "energy": e64, "norm_drift": abs(n64 - 1.0)},
+            "c64_infidelity_vs_c128": inf, "c64_energy_error_vs_c128": abs(e64 - e128),
+            "reference": "the complex128 GPU run of the same step (FP64-class reference)"}
+
+
+def shard_measure(capi, torch, barrier, n: int = 24, terms: int = 2000, seed: int = 1, gs=(1, 2, 3)):
+    """The global-qubit sharded path on one GPU: the first Trotter step of the
+    n = 24 workload (2000 rotations, complex64) with the state split into 2^g
+    slices that all live on this GPU (InProcessComm: an exchange is a device
+    copy standing in for the transfer between GPUs), then <H>.  Wall time with
+    the stream synchronised, against the same step on one unsharded state;
+    counts the exchanges and the rotations run on pair states."""
+    from paper_2602_09020_gb300.shard import InProcessComm, ShardedState
+    ham = synth.jw_hamiltonian(n, terms, seed)
+    rx, rz, rt = capi.trotter_expand(ham.x, ham.z, ham.c, 0.05, 1, 1, False)
+    basis = synth.hartree_fock_index(n // 2)
+    out = {"n": n, "dtype": "c64", "rotations": len(rt), "rows": []}
+    sv = capi.sv_alloc(n, "c64", int(torch.cuda.current_stream().cuda_stream))
+    try:
+        for rep in range(2):
+            capi.sv_set_basis_state(sv, basis)
+            barrier()
+            t0 = time.perf_counter()
+            capi.apply_pauli_rotations(sv, rx, rz, rt)
+            e1, _ = capi.expval_pauli_sum(sv, ham.x, ham.z, ham.c)
+            barrier()
+            single = time.perf_counter() - t0
+    finally:
+        capi.sv_free(sv)
+    out["unsharded_ms"] = 1000.0 * single
+    for g in gs:
+        comm = InProcessComm(1 << g)
+        st = ShardedState(n, "c64", g, comm)
+        try:
+            steps = capi.shard_rotations(n, g, 0, rx, rz, rt)[0]
+            for rep in range(2):
+                st.set_basis_state(basis)
+                barrier()
+                t0 = time.perf_counter()
+                st.apply_pauli_rotations(rx, rz, rt)
+                e, _ = st.expval_pauli_sum(ham.x, ham.z, ham.c)
+                barrier()
+                el = time.perf_counter() - t0
+        finally:
+            st.close()
+        pair_rot = sum(c for k, _, _, c in steps if k == 1)
+        out["rows"].append({"global_qubits": g, "slices": 1 << g, "ms": 1000.0 * el,
+                            "rotations_per_s": len(rt) / el, "rotation_steps": len(steps),
+                            "exchanges_for_rotations": sum(1 for k, *_ in steps if k == 1),
+                            "rotations_on_pair_states": pair_rot, "energy": e,
+                            "energy_minus_unsharded": e - e1})
+    return out
 
 
 def locality_measure(capi, torch, n: int, dtype: str, barrier, terms: int = 100,
@@ -692,8 +909,16 @@ def batch_measure(capi, torch, stream, sh, barrier, reps: int = 3):
         barrier()
         el2 = (time.perf_counter() - t0) / reps
         launches = sum(capi.plan_stats(p)[1] for p in plans)
+        # algorithmic bytes of the persistent launch: every pass of every state
+        # reads and writes that state once (2 x 8 x 2^n bytes)
+        nbytes = sum(capi.plan_stats(p)[1] * 2.0 * 8.0 * (1 << c.n) for p, c in zip(plans, wl))
+        pk = peaks()
         out.update({"per_state_ms": 1000 * el2, "per_state_rotations_per_s": total / el2,
-                    "per_state_launches": launches, "speedup": el2 / el})
+                    "per_state_launches": launches, "speedup": el2 / el,
+                    "algorithmic_bytes": nbytes, "persistent_gbs": nbytes / el / 1e9,
+                    "persistent_hbm_frac": nbytes / el / 1e9 / pk["hbm_gbs"],
+                    "per_state_hbm_frac": nbytes / el2 / 1e9 / pk["hbm_gbs"],
+                    "hbm_peak": pk["hbm_gbs"], "peak_source": pk["source"]})
     finally:
         for p in plans:
             capi.plan_free(p)

@@ -1560,6 +1560,7 @@ int na_plan(const sv_state *sv, const uint64_t *x, const uint64_t *z, const doub
   return nr;
 }
 
+// caller holds g_na_mutex
 int na_device_scratch(void **out) {
   int dev = 0;
   PR_CUDA(cudaGetDevice(&dev));
@@ -1627,10 +1628,12 @@ extern "C" int expval_pauli_sum_noalloc(sv_state *sv, const uint64_t *x, const u
   if (rc) return rc;
   for (size_t j = 0; j < count; ++j)
     if (!std::isfinite(coeff[j])) return fail(SV_EINVAL, "coefficient %zu is not finite", j);
+  // the lock also covers the per-device cache of the scratch address, so two
+  // threads making their first call on a device do not race on it
+  std::lock_guard<std::mutex> lock(g_na_mutex);
   void *scratch = nullptr;
   rc = na_device_scratch(&scratch);
   if (rc) return rc;
-  std::lock_guard<std::mutex> lock(g_na_mutex);
   const int D = std::min(kExpD, sv->n);
   const int nr = na_plan(sv, x, z, coeff, (int)count, D);
   if (nr < 0) return nr;

@@ -124,20 +124,33 @@ class PauliRotationEnergy(torch.autograd.Function):
     """E(theta) = <psi|H|psi>, psi = R_{M-1}(theta_{M-1}) ... R_0(theta_0) psi0.
 
     forward(theta, psi0, x, z, hx, hz, hc) -> 0-dim float64 tensor; theta is a
-    1-D float64 tensor (any device; it is read on the host).  The gradient is
-    the FP64 adjoint sweep of the library.
+    1-D float64 tensor (any device; it is read on the host).  Forward applies
+    the rotations to a copy of psi0 (apply_pauli_rotations) and reduces <H>
+    (expval_pauli_sum); psi0 is not modified.  Backward runs the library's FP64
+    adjoint sweep (rotation_grads) from psi0 for dE/dtheta, so an evaluation
+    without a backward pass (e.g. under torch.no_grad) pays for no gradient.
+    psi0 must not change between forward and backward.
     """
 
     @staticmethod
     def forward(ctx, theta, psi0: StateVector, x, z, hx, hz, hc):
-        th = theta.detach().to("cpu", torch.float64).numpy()
-        e, g = capi.rotation_grads(psi0.handle, x, z, th, hx, hz, hc)
-        ctx.save_for_backward(torch.from_numpy(g).to(theta.device))
+        th = theta.detach().to("cpu", torch.float64).numpy().copy()
+        dt = "c128" if psi0.dtype == capi.SV_C128 else "c64"
+        work = StateVector(psi0.n, dt, device=psi0.amps.device)
+        try:
+            work.copy_from(psi0)
+            work.apply_pauli_rotations(x, z, th)
+            e, _ = work.expval_pauli_sum(hx, hz, hc)
+        finally:
+            work.close()
+        ctx.psi0, ctx.args, ctx.theta = psi0, (x, z, hx, hz, hc), th
         return torch.tensor(e, dtype=torch.float64, device=theta.device)
 
     @staticmethod
     def backward(ctx, grad_out):
-        (g,) = ctx.saved_tensors
+        x, z, hx, hz, hc = ctx.args
+        _, g = capi.rotation_grads(ctx.psi0.handle, x, z, ctx.theta, hx, hz, hc)
+        g = torch.from_numpy(g).to(grad_out.device)
         return grad_out * g, None, None, None, None, None, None
 
 

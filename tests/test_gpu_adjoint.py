@@ -90,3 +90,28 @@ def test_autograd_function(orc):
     e_ref, g_ref = orc.grad_param_shift(n, orc.basis_state(n, 7), x, z, th, obs.x, obs.z, obs.c)
     assert abs(e.item() - e_ref) < 1e-11
     assert np.max(np.abs(theta.grad.numpy() - g_ref)) < 1e-10 * max(1.0, np.abs(g_ref).max())
+
+
+def test_autograd_forward_alone_and_psi0_unchanged(orc):
+    """Forward is E only (rotations on a copy, then <H>): under no_grad it gives
+    the oracle's energy, leaves psi0 as it was, and a later backward still
+    gives the oracle's parameter-shift gradient."""
+    torch = pytest.importorskip("torch")
+    from paper_2602_09020_gb300.torch_api import StateVector, pauli_rotation_energy
+    n, n_rot = 7, 30
+    x, z, th, obs = synth.adjoint_workload(n, n_rot, 25, seed=8)
+    basis = synth.hartree_fock_index(3)
+    psi0 = StateVector(n, "c128").set_basis_state(basis)
+    psi0.frame_apply_pauli("X", 4)
+    before = psi0.to_host(False)
+    theta = torch.tensor(th, dtype=torch.float64, requires_grad=True)
+    start = orc.gate(orc.basis_state(n, basis), n, "x", 4)
+    e_ref, g_ref = orc.grad_param_shift(n, start, x, z, th, obs.x, obs.z, obs.c)
+    with torch.no_grad():
+        e0 = pauli_rotation_energy(theta, psi0, x, z, obs.x, obs.z, obs.c)
+    assert abs(e0.item() - e_ref) < 1e-11
+    np.testing.assert_array_equal(psi0.to_host(False), before)
+    e = pauli_rotation_energy(theta, psi0, x, z, obs.x, obs.z, obs.c)
+    e.backward()
+    assert abs(e.item() - e_ref) < 1e-11
+    assert np.max(np.abs(theta.grad.numpy() - g_ref)) < 1e-10 * max(1.0, np.abs(g_ref).max())

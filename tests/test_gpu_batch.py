@@ -2,7 +2,7 @@
 
 Checks: every state of an uneven batch equals the same plan applied on its own
 (bitwise: each coset's arithmetic does not depend on which CTA runs it) and
-matches the oracle; CUDA-graph replay gives the same result as a direct launch;
+every one matches the oracle; CUDA-graph replay gives the same result as a direct launch;
 states large enough to span several CTAs are exercised (their CTAs meet at
 bounded barriers); and the failure path: when one CTA skips a barrier arrival,
 its peers' waits run out, the call returns SV_ETIMEOUT and the context stays
@@ -66,7 +66,7 @@ def test_batch_matches_single_launches_and_oracle(orc, dtype):
     for a, b, c in zip(single, direct, graph):
         np.testing.assert_array_equal(a, b)
         np.testing.assert_array_equal(a, c)
-    for k in (0, 3):
+    for k in range(len(probs)):  # every state of the batch against the oracle
         n, rx, rz, rt, psi0 = probs[k]
         want = orc.apply_rotations(psi0.astype(np.complex128).copy(), n, rx, rz, rt)
         if dtype == "c128":

@@ -6,8 +6,8 @@ take the device-wide synchronisation an allocation can cause, hosts that
 forbid allocation after start-up.  For them the library offers one entry point
 that uses a fixed scratch array inside the library instead of allocating.
 These tests call it through the C ABI and check it against the regular
-expval_pauli_sum, twice in a row (the scratch keeps the previous call's
-contents, which must not leak into the next result).  This file is collected
+expval_pauli_sum and against the oracle, twice in a row (the scratch keeps
+the previous call's contents, which must not leak into the next result).  This file is collected
 last so that a run stopping at the first failure has run everything else.
 """
 import ctypes
@@ -26,7 +26,7 @@ def _tol(c):
 
 
 @pytest.mark.parametrize("dtype,n", [("c128", 12), ("c64", 12), ("c128", 3), ("c64", 20)])
-def test_noalloc_matches_expval_twice(dtype, n):
+def test_noalloc_matches_expval_twice(orc, dtype, n):
     ham = synth.jw_hamiltonian(n, 300, 5) if n >= 4 else None
     if ham is None:
         x, z = random_paulis(n, 20, seed=1, diag_frac=0.3)
@@ -39,9 +39,16 @@ def test_noalloc_matches_expval_twice(dtype, n):
         capi.sv_from_host(sv, psi.astype(np.complex64 if dtype == "c64" else np.complex128))
         capi.frame_apply_pauli(sv, "Y", 1)
         e_ref, n_ref = capi.expval_pauli_sum(sv, x, z, c)
+        # the oracle on the same state: the stored amplitudes (rounded to the
+        # handle's precision) with the frame's Y on qubit 1 applied as a gate
+        stored = psi.astype(np.complex64 if dtype == "c64" else np.complex128).astype(np.complex128)
+        e_orc = orc.expval(orc.gate(stored.copy(), n, "y", 1), n, x, z, c)
+        assert abs(e_ref - e_orc) <= _tol(c), (e_ref, e_orc)
+        assert abs(n_ref - orc.norm2(stored, n)) <= 1e-13
         for _ in range(2):
             e, nrm = capi.expval_pauli_sum_noalloc(sv, x, z, c)
             assert abs(e - e_ref) <= _tol(c), (e, e_ref)
+            assert abs(e - e_orc) <= _tol(c), (e, e_orc)
             assert abs(nrm - n_ref) <= 1e-13
         # a different, smaller request right after a larger one
         e1, _ = capi.expval_pauli_sum(sv, x[:7], z[:7], c[:7])
