@@ -86,15 +86,18 @@ def peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-# source files that define each traced kernel family: a stored ncu traffic
-# figure counts only while these are unchanged since the capture
-KERNEL_SOURCES = {"k_coset": ("kernels.cuh", "rotate.cu"), "k_diag_sum": ("kernels.cuh", "rotate.cu"),
-                  "k_expval": ("reduce.cu",)}
+# source files that define each traced kernel family, per precision: a stored
+# ncu traffic figure counts only while these are unchanged since the capture
+KERNEL_SOURCES = {("k_coset", "c64"): ("kernels.cuh", "rotate.cu"),
+                  ("k_coset", "c128"): ("coset_fx.cuh", "kernels.cuh", "rotate.cu"),
+                  ("k_diag_sum", "c64"): ("kernels.cuh", "rotate.cu"),
+                  ("k_diag_sum", "c128"): ("kernels.cuh", "rotate.cu"),
+                  ("k_expval", "c64"): ("reduce.cu",), ("k_expval", "c128"): ("reduce.cu",)}
 
 
-def kernel_source_digest(name: str):
-    for prefix, files in KERNEL_SOURCES.items():
-        if name.startswith(prefix):
+def kernel_source_digest(name: str, dtype: str):
+    for (prefix, dt), files in KERNEL_SOURCES.items():
+        if name.startswith(prefix) and dt == dtype:
             h = hashlib.sha256()
             for f in files:
                 with open(os.path.join(ROOT, "paper_2602_09020_gb300", "csrc", f), "rb") as fh:
@@ -112,7 +115,7 @@ def ncu_traffic(name: str, dtype: str, n: int):
         return None
     with open(p) as fh:
         entry = json.load(fh).get(f"{name}/{dtype}/n{n}")
-    if not entry or entry.get("sources_sha256") != kernel_source_digest(name):
+    if not entry or entry.get("sources_sha256") != kernel_source_digest(name, dtype):
         return None
     return entry["dram_bytes_per_launch"]
 
