@@ -22,11 +22,13 @@
 // angle reduction, T clamped to |T| < 2^62) split as T = th * 2^31 + tl with
 // 0 <= tl < 2^31, and likewise A = ah * 2^31 + al; then
 //   A T / 2^62 = ah th + (ah tl + al th) / 2^31 + al tl / 2^62,
-// three 32 x 32 -> 64-bit integer multiply-adds (fx_madd, fx_msub).  The last term (in [0, 1))
-// is replaced by its mean together with the rounding of the shift, so a
-// product is within 1.25 units of 2^-S of the exact one and unbiased.  Per
-// coset the resolution is 2^-58 of the largest component or finer, which is
-// finer than the 2^-53 relative rounding of the FP64 value the pass stores.
+// three 32 x 32 -> 64-bit integer multiplies (fx_prod).  The last term (in
+// [0, 1)) is dropped and the shift floors, so a product is low by less than 2
+// units of 2^-S, by 3/4 of a unit on average; every update adds a product (a
+// subtraction adds the product with -T), so the run adds that mean back to every
+// component once, at the end.  Per coset the resolution is 2^-58 of the largest
+// component or finer, which is finer than the 2^-53 relative rounding of the
+// FP64 value the pass stores.
 //
 // Conversions use the IEEE-754 binary64 layout directly (sign, 11-bit biased
 // exponent, 52-bit fraction with an implicit leading one), so no conversion
@@ -60,15 +62,19 @@ __device__ __forceinline__ void fx_limbs(int64_t T, int32_t &th, int32_t &tl) {
   tl = (int32_t)(T & 0x7fffffffLL);
 }
 
-// acc + B * T / 2^62 and acc - B * T / 2^62 for |B| < 2^61 and T = th * 2^31 + tl,
-// 0 <= tl < 2^31: with B = bh * 2^31 + bl (0 <= bl < 2^31),
-//   B T / 2^62 = bh th + (bh tl + bl th) / 2^31 + bl tl / 2^62.
-// The middle sum gets 3 * 2^29 (the mean of the dropped last term, 1/4, plus
-// the shift's floor, 1/2) before its arithmetic shift.  Written as PTX: each
+// B * T / 2^62, truncated, for |B| < 2^61 and T = th * 2^31 + tl, 0 <= tl < 2^31:
+// with B = bh * 2^31 + bl (0 <= bl < 2^31),
+//   B T / 2^62 = bh th + (bh tl + bl th) / 2^31 + bl tl / 2^62,
+// computed as bh th + floor((bh tl + bl th) / 2^31): the last term (in [0, 1))
+// is dropped and the shift floors, so the result is below the exact product by
+// less than 2 units of 2^-S, by 3/4 of a unit on average.  The pass adds that
+// mean back once per component at the end of the run (every component receives
+// exactly one product per rotation), not per product.  Written as PTX: each
 // partial product is one 32 x 32 -> 64-bit multiply (mul.wide.s32) and the sums
-// are plain 64-bit adds, the form that measured fastest on GB300 (19 % above
-// multiply-adds with a 64-bit addend).
-__device__ __forceinline__ int64_t fx_prod(int64_t b, int32_t th, int32_t tl, int64_t bias) {
+// are plain 64-bit adds, the form that measured fastest on GB300 (a rounding
+// constant added per product cost 12 % of the multiply-add rate, 64-bit
+// multiply-add addends another 19 %).
+__device__ __forceinline__ int64_t fx_prod(int64_t b, int32_t th, int32_t tl) {
   int64_t r;
   asm("{\n\t"
       ".reg .b32 bl, bh;\n\t"
@@ -79,20 +85,13 @@ __device__ __forceinline__ int64_t fx_prod(int64_t b, int32_t th, int32_t tl, in
       "mul.wide.s32 m, bh, %3;\n\t"
       "mul.wide.s32 n, bl, %2;\n\t"
       "add.s64 m, m, n;\n\t"
-      "add.s64 m, m, %4;\n\t"
       "shr.s64 m, m, 31;\n\t"
       "mul.wide.s32 n, bh, %2;\n\t"
       "add.s64 %0, n, m;\n\t"
       "}"
       : "=l"(r)
-      : "l"(b), "r"(th), "r"(tl), "l"(bias));
+      : "l"(b), "r"(th), "r"(tl));
   return r;
-}
-__device__ __forceinline__ int64_t fx_madd(int64_t acc, int64_t b, int32_t th, int32_t tl, int64_t bias) {
-  return acc + fx_prod(b, th, tl, bias);
-}
-__device__ __forceinline__ int64_t fx_msub(int64_t acc, int64_t b, int32_t th, int32_t tl, int64_t bias) {
-  return acc - fx_prod(b, th, tl, bias);
 }
 
 // binary64 -> A = round(a * 2^S), with kbase = 1085 - S; needs 1085 - S - e >= 2
@@ -122,33 +121,37 @@ __device__ __forceinline__ double fx_out(int64_t a, int ebase) {
 
 // Apply one rotation with coset coordinates U (compile-time) to V cosets;
 // sg[v] is the sign bit (-1)^{popc(rep_v & z)}, bit l of zt the element's.
+// (th0, tl0) are the limbs of +T, (th1, tl1) those of -T.  Every update is an
+// addition of a truncated product (a subtraction adds the product with -T), so
+// every product is low by the same 3/4 unit on average (see fx_prod).
 template <int D, int V, int U, int IMAG>
 __device__ __forceinline__ void apply_fx(int64_t (&re)[V][1 << D], int64_t (&im)[V][1 << D], const int (&sg)[V],
                                          uint32_t zt, int32_t th0, int32_t tl0, int32_t th1, int32_t tl1) {
-  const int64_t bias = int64_t(3) << 29;
 #pragma unroll
   for (int v = 0; v < V; ++v) {
 #pragma unroll
     for (int l = 0; l < (1 << D); ++l) {
       const int s = sg[v] ^ (int)((zt >> l) & 1u);
-      const int32_t th = s ? th1 : th0, tl = s ? tl1 : tl0;
+      // limbs of +-T for the element's sign s, and of the opposite sign
+      const int32_t tp = s ? th1 : th0, lp = s ? tl1 : tl0;
+      const int32_t tn = s ? th0 : th1, ln = s ? tl0 : tl1;
       if (U == 0) {
         const int64_t r = re[v][l], i = im[v][l];
-        re[v][l] = fx_msub(r, i, th, tl, bias);
-        im[v][l] = fx_madd(i, r, th, tl, bias);
+        re[v][l] = r + fx_prod(i, tn, ln);
+        im[v][l] = i + fx_prod(r, tp, lp);
       } else if ((l ^ U) > l) {
         const int m = l ^ U;
         const int64_t rl = re[v][l], il = im[v][l], rm = re[v][m], iv = im[v][m];
         if (IMAG) {
-          re[v][l] = fx_msub(rl, iv, th, tl, bias);
-          im[v][l] = fx_madd(il, rm, th, tl, bias);
-          re[v][m] = fx_msub(rm, il, th, tl, bias);
-          im[v][m] = fx_madd(iv, rl, th, tl, bias);
+          re[v][l] = rl + fx_prod(iv, tn, ln);
+          im[v][l] = il + fx_prod(rm, tp, lp);
+          re[v][m] = rm + fx_prod(il, tn, ln);
+          im[v][m] = iv + fx_prod(rl, tp, lp);
         } else {
-          re[v][l] = fx_madd(rl, rm, th, tl, bias);
-          im[v][l] = fx_madd(il, iv, th, tl, bias);
-          re[v][m] = fx_msub(rm, rl, th, tl, bias);
-          im[v][m] = fx_msub(iv, il, th, tl, bias);
+          re[v][l] = rl + fx_prod(rm, tp, lp);
+          im[v][l] = il + fx_prod(iv, tp, lp);
+          re[v][m] = rm + fx_prod(rl, tn, ln);
+          im[v][m] = iv + fx_prod(il, tn, ln);
         }
       }
     }
@@ -185,7 +188,7 @@ __device__ __forceinline__ void dispatch_fx(uint32_t code, int64_t (&re)[V][1 <<
 template <typename Idx, int D>
 __host__ __device__ constexpr size_t ws_coset_fx() {
   return ((sizeof(RotFx<Idx>) * kMaxRunRots + sizeof(Idx) * (1u << D) + 15) & ~size_t(15)) +
-         sizeof(uint32_t) * (kThreads / 32);
+         2 * sizeof(uint32_t) * (kThreads / 32);
 }
 
 // One CTA's share of a fused complex128 run in fixed point.  The run must hold
@@ -233,10 +236,22 @@ __device__ __forceinline__ void body_coset_fx(double2 *__restrict__ amp, Idx n_c
   uint32_t base = 0;
   for (int w = 0; w < warp; ++w) base += swarp[w];
   c += base;
+  uint32_t total = 0;  // growth over the whole run
+  for (int w = 0; w < kThreads / 32; ++w) total += swarp[w];
+  // mean correction of the truncated products (fx_prod): 3/4 of a unit per
+  // product, one product per component and rotation; what a rotation adds is
+  // halved with the components at every later halving.  Units of 2^-20 unit.
+  uint32_t corr = 0;
   if (j < count) {
     rec.halve = (int32_t)((c >> kGrowthFrac) - ((c - g) >> kGrowthFrac));
     srot[j] = rec;
+    // halvings at this rotation (after its products) and at later ones
+    const uint32_t later = (total >> kGrowthFrac) - ((c - g) >> kGrowthFrac);
+    corr = later < 31 ? (3u << 18) >> later : 0u;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) corr += __shfl_down_sync(0xffffffffu, corr, o);
+  if (lane == 0) swarp[kThreads / 32 + warp] = corr;
   if (threadIdx.x < E) {
     uint64_t s = 0;
     for (int b = 0; b < D; ++b)
@@ -244,6 +259,9 @@ __device__ __forceinline__ void body_coset_fx(double2 *__restrict__ amp, Idx n_c
     soff[threadIdx.x] = (Idx)s;
   }
   __syncthreads();
+  uint32_t corr_sum = 0;
+  for (int w = 0; w < kThreads / 32; ++w) corr_sum += swarp[kThreads / 32 + w];
+  const int64_t bias = (int64_t)((corr_sum + (1u << 19)) >> 20);  // units added to every component
 
   // headroom: the coset's 2-norm is at most 2^((D+1)/2) times its largest
   // component, and the growth between halvings stays below one bit
@@ -304,6 +322,13 @@ __device__ __forceinline__ void body_coset_fx(double2 *__restrict__ amp, Idx n_c
           }
       }
     }
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int l = 0; l < E; ++l) {
+        re[v][l] += bias;
+        im[v][l] += bias;
+      }
     // the fold (a complex factor, last pass of a plan) in FP64 after the
     // conversion; two separate store loops keep the FP64 multiplies out of the
     // passes without a fold
