@@ -332,7 +332,11 @@ int apply_pauli_sum(sv_state *dst, sv_state *src, const uint64_t *x, const uint6
  * g_j = Im <lambda|P_j|phi_j>, phi <- R_j^dag phi, lambda <- R_j^dag lambda,
  * walked in fused runs (consecutive rotations whose x-masks span <= 3
  * dimensions share one pass over phi and lambda).  Precision: complex128
- * computes in FP64; complex64 applies the rotations to phi and lambda in FP32
+ * applies the rotations in 64-bit fixed point with one exponent per coset of
+ * each vector (resolution 2^-58 of the coset's largest component or finer) and
+ * forms each coset's share of a gradient from fixed-point products summed
+ * exactly, then in FP64 (a rotation of a diagonal stretch with |angle| > pi/2
+ * takes an FP64 pass of its own); complex64 applies the rotations to phi and lambda in FP32
  * and sums every gradient term in FP64 (each FP32 term widened exactly; a term
  * below 1.2e-38 in magnitude counts as zero), and lambda = H psi sums each
  * element's coefficients exactly in 64-bit fixed point before one FP64

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <vector>
 
+#include "fixed64.cuh"
 #include "internal.h"
 
 namespace pr {
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(kThreads)
 // One read and one write of phi and lambda per run instead of per rotation.
 
 constexpr int kAdjD = 3;     // run span dimension: 8 elements per coset
+constexpr double kHalfPi = 1.5707963267948966;
 constexpr int kAdjRun = 20;  // rotations per run (shared-memory accumulators)
 
 struct AdjRotDev {
@@ -334,6 +336,260 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// ---- complex128 backward runs in 64-bit fixed point ---------------------------
+//
+// The same run as k_adjoint_run<double> on the integer pipes (the FP64 version
+// is bound by GB300's narrow FP64 pipe).  A thread converts its coset of phi
+// and of lambda with one exponent each (fixed64.cuh: block floating point, the
+// coset's 2-norm below 2^61); R_j^dag = cos(beta/2) (1 + i t P) is applied in tan
+// form with truncated products, one per component and rotation, whose mean the
+// run adds back at the end; both vectors are halved whenever the known growth
+// sqrt(1 + t^2) per rotation passes a whole bit.  A rotation's share of
+// Im<lambda|P|phi> over the coset is a sum of products of a lambda and a phi
+// component (truncated, at the scale 2^(62 - S_phi - S_lambda)), summed exactly
+// in 64 bits -- by Cauchy-Schwarz the sum stays below 2^61 -- then converted to
+// FP64 once per coset and rotation and added to the FP64 accumulator.
+
+struct AdjRotFx {
+  uint64_t z;
+  uint32_t zt;
+  int32_t uk;     // u * 4 + nY mod 4
+  int32_t th[2];  // limbs of +T and -T, T = round(t 2^62)
+  int32_t tl[2];
+  int32_t halve;  // 1: halve both vectors after this rotation
+  int32_t pad;
+};
+
+// Im(conj(a) i^K b) from truncated products a_c b_c' / 2^62; b by its limbs
+template <int K>
+__device__ __forceinline__ int64_t fx_im_conj_ipow(int64_t ax, int64_t ay, int32_t bxh, int32_t bxl, int32_t byh,
+                                                   int32_t byl) {
+  if constexpr ((K & 3) == 0) return fx_prod(ax, byh, byl) - fx_prod(ay, bxh, bxl);
+  if constexpr ((K & 3) == 1) return fx_prod(ax, bxh, bxl) + fx_prod(ay, byh, byl);
+  if constexpr ((K & 3) == 2) return fx_prod(ay, bxh, bxl) - fx_prod(ax, byh, byl);
+  return -(fx_prod(ax, bxh, bxl) + fx_prod(ay, byh, byl));
+}
+
+// v_e += t_m i^{K+1} v_m and v_m += t_e i^{K+1} v_e from the old values; the
+// limbs (p: +t, n: -t) of t_e and t_m carry each element's sign
+template <int K>
+__device__ __forceinline__ void fx_adj_pair(int64_t (&ve)[2], int64_t (&vm)[2], int32_t tpe, int32_t lpe,
+                                            int32_t tne, int32_t lne, int32_t tpm, int32_t lpm, int32_t tnm,
+                                            int32_t lnm) {
+  constexpr int k1 = (K + 1) & 3;
+  const int64_t ex = ve[0], ey = ve[1], mx = vm[0], my = vm[1];
+  if constexpr (k1 == 0) {
+    ve[0] = ex + fx_prod(mx, tpm, lpm);
+    ve[1] = ey + fx_prod(my, tpm, lpm);
+    vm[0] = mx + fx_prod(ex, tpe, lpe);
+    vm[1] = my + fx_prod(ey, tpe, lpe);
+  } else if constexpr (k1 == 1) {  // i v = (-v.y, v.x)
+    ve[0] = ex + fx_prod(my, tnm, lnm);
+    ve[1] = ey + fx_prod(mx, tpm, lpm);
+    vm[0] = mx + fx_prod(ey, tne, lne);
+    vm[1] = my + fx_prod(ex, tpe, lpe);
+  } else if constexpr (k1 == 2) {  // -v
+    ve[0] = ex + fx_prod(mx, tnm, lnm);
+    ve[1] = ey + fx_prod(my, tnm, lnm);
+    vm[0] = mx + fx_prod(ex, tne, lne);
+    vm[1] = my + fx_prod(ey, tne, lne);
+  } else {  // -i v = (v.y, -v.x)
+    ve[0] = ex + fx_prod(my, tpm, lpm);
+    ve[1] = ey + fx_prod(mx, tnm, lnm);
+    vm[0] = mx + fx_prod(ey, tpe, lpe);
+    vm[1] = my + fx_prod(ex, tne, lne);
+  }
+}
+
+// One rotation of the run on a coset of phi (P) and lambda (L); returns the
+// coset's share of Im<lambda|P_j|phi> in units of 2^(62 - S_phi - S_lambda).
+template <int U, int K>
+__device__ __forceinline__ int64_t adj_rot_fx(int64_t (&P)[1 << kAdjD][2], int64_t (&L)[1 << kAdjD][2],
+                                              const AdjRotFx &r, int sig) {
+  constexpr int E = 1 << kAdjD;
+  const int32_t th0 = r.th[0], tl0 = r.tl[0], th1 = r.th[1], tl1 = r.tl[1];
+  int64_t g = 0;
+  if constexpr (U == 0) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int neg = (sig ^ (int)(r.zt >> e)) & 1;
+      const int32_t tp = neg ? th1 : th0, lp = neg ? tl1 : tl0;  // limbs of t_s
+      const int32_t tn = neg ? th0 : th1, ln = neg ? tl0 : tl1;  // limbs of -t_s
+      int32_t pxh, pxl, pyh, pyl;
+      fx_limbs(P[e][0], pxh, pxl);
+      fx_limbs(P[e][1], pyh, pyl);
+      const int64_t v = fx_im_conj_ipow<0>(L[e][0], L[e][1], pxh, pxl, pyh, pyl);
+      g += neg ? -v : v;
+      const int64_t px = P[e][0], py = P[e][1], lx = L[e][0], ly = L[e][1];
+      P[e][0] = px + fx_prod(py, tn, ln);
+      P[e][1] = py + fx_prod(px, tp, lp);
+      L[e][0] = lx + fx_prod(ly, tn, ln);
+      L[e][1] = ly + fx_prod(lx, tp, lp);
+    }
+  } else {
+    constexpr int H = adj_high_bit(U);
+#pragma unroll
+    for (int q = 0; q < E / 2; ++q) {
+      const int e = ((q >> H) << (H + 1)) | (q & ((1 << H) - 1));
+      const int m = e ^ U;
+      const int ne = (sig ^ (int)(r.zt >> e)) & 1, nm = (sig ^ (int)(r.zt >> m)) & 1;
+      int32_t exh, exl, eyh, eyl, mxh, mxl, myh, myl;
+      fx_limbs(P[e][0], exh, exl);
+      fx_limbs(P[e][1], eyh, eyl);
+      fx_limbs(P[m][0], mxh, mxl);
+      fx_limbs(P[m][1], myh, myl);
+      const int64_t ge = fx_im_conj_ipow<K>(L[e][0], L[e][1], mxh, mxl, myh, myl);
+      const int64_t gm = fx_im_conj_ipow<K>(L[m][0], L[m][1], exh, exl, eyh, eyl);
+      g += (nm ? -ge : ge) + (ne ? -gm : gm);
+      const int32_t tpe = ne ? th1 : th0, lpe = ne ? tl1 : tl0, tne = ne ? th0 : th1, lne = ne ? tl0 : tl1;
+      const int32_t tpm = nm ? th1 : th0, lpm = nm ? tl1 : tl0, tnm = nm ? th0 : th1, lnm = nm ? tl0 : tl1;
+      fx_adj_pair<K>(P[e], P[m], tpe, lpe, tne, lne, tpm, lpm, tnm, lnm);
+      fx_adj_pair<K>(L[e], L[m], tpe, lpe, tne, lne, tpm, lpm, tnm, lnm);
+    }
+  }
+  return g;
+}
+
+#define PR_ADJ_FX_CASE(UK) \
+  case UK: return adj_rot_fx<((UK) >> 2), ((UK)&3)>(P, L, r, sig);
+
+__device__ __forceinline__ int64_t adj_dispatch_fx(int uk, int64_t (&P)[1 << kAdjD][2], int64_t (&L)[1 << kAdjD][2],
+                                                   const AdjRotFx &r, int sig) {
+  switch (uk) {
+    PR_ADJ_FX_CASE(0)
+    PR_ADJ_FX_CASE(4) PR_ADJ_FX_CASE(5) PR_ADJ_FX_CASE(6) PR_ADJ_FX_CASE(7)
+    PR_ADJ_FX_CASE(8) PR_ADJ_FX_CASE(9) PR_ADJ_FX_CASE(10) PR_ADJ_FX_CASE(11)
+    PR_ADJ_FX_CASE(12) PR_ADJ_FX_CASE(13) PR_ADJ_FX_CASE(14) PR_ADJ_FX_CASE(15)
+    PR_ADJ_FX_CASE(16) PR_ADJ_FX_CASE(17) PR_ADJ_FX_CASE(18) PR_ADJ_FX_CASE(19)
+    PR_ADJ_FX_CASE(20) PR_ADJ_FX_CASE(21) PR_ADJ_FX_CASE(22) PR_ADJ_FX_CASE(23)
+    PR_ADJ_FX_CASE(24) PR_ADJ_FX_CASE(25) PR_ADJ_FX_CASE(26) PR_ADJ_FX_CASE(27)
+    PR_ADJ_FX_CASE(28) PR_ADJ_FX_CASE(29) PR_ADJ_FX_CASE(30) PR_ADJ_FX_CASE(31)
+    default: return 0;
+  }
+}
+
+// two CTAs per SM (128 registers, a few spilled) measured faster than one
+// with 254 registers: 6.86 against 7.04 ms for the n = 20 gradient workload
+__global__ void __launch_bounds__(kThreads, 2)
+    k_adjoint_run_fx(double2 *__restrict__ phi, double2 *__restrict__ lam, uint64_t n_cosets,
+                     const __grid_constant__ AdjRunDev run, int row_stride, double *__restrict__ partials) {
+  static_assert(kAdjRun <= 32, "the run's records are set up by one warp");
+  constexpr int E = 1 << kAdjD;
+  constexpr int kHead = (kAdjD + 2) / 2 + 1;  // as in the rotation pass (coset_fx.cuh)
+  __shared__ double sacc[kAdjRun][kThreads];  // one column per thread
+  __shared__ AdjRotFx srot[kAdjRun];
+  __shared__ int64_t s_bias;
+  for (int j = 0; j < kAdjRun; ++j) sacc[j][threadIdx.x] = 0.0;
+  const int count = run.count;
+  if (threadIdx.x < 32) {
+    // limbs of +-T, growth bound ceil(log2(1 + t^2) / 2 * 2^20) + 1, halvings,
+    // and the mean correction of the truncated products (3/4 unit per product,
+    // halved at later halvings; units of 2^-20 unit)
+    const int j = threadIdx.x;
+    uint32_t g = 0;
+    AdjRotFx rec = {};
+    if (j < count) {
+      const AdjRotDev r = run.rot[j];
+      long long T = __double2ll_rn(r.t * kTwo62);
+      T = T > kTMax ? kTMax : (T < -kTMax ? -kTMax : T);
+      fx_limbs(T, rec.th[0], rec.tl[0]);
+      fx_limbs(-T, rec.th[1], rec.tl[1]);
+      rec.z = r.z;
+      rec.zt = r.zt;
+      rec.uk = r.u * 4 + r.ny;
+      const float tf = (float)r.t;
+      g = (uint32_t)ceilf(0.5f * __log2f(1.0f + tf * tf) * (float)(1 << kGrowthFrac)) + 1u;
+    }
+    uint32_t c = g;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, c, o);
+      if (j >= o) c += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, c, 31);
+    uint32_t corr = 0;
+    if (j < count) {
+      rec.halve = (int32_t)((c >> kGrowthFrac) - ((c - g) >> kGrowthFrac));
+      srot[j] = rec;
+      const uint32_t later = (total >> kGrowthFrac) - ((c - g) >> kGrowthFrac);
+      corr = later < 31 ? (3u << 18) >> later : 0u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) corr += __shfl_down_sync(0xffffffffu, corr, o);
+    if (j == 0) s_bias = (int64_t)((corr + (1u << 19)) >> 20);
+  }
+  __syncthreads();
+  const int64_t bias = s_bias;
+  const double sc = run.scale;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t cs = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; cs < n_cosets; cs += stride) {
+    uint64_t rep = cs;
+#pragma unroll
+    for (int b = 0; b < kAdjD; ++b) {
+      const int pv = run.piv[b];
+      rep = ((rep >> pv) << (pv + 1)) | (rep & ((1ULL << pv) - 1));
+    }
+    int64_t P[E][2], L[E][2];
+    int Sp, Sl;
+    {
+      double2 a[E], b[E];
+      int ep = 0, el = 0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        a[e] = phi[rep ^ run.soff[e]];
+        b[e] = lam[rep ^ run.soff[e]];
+        ep = max(ep, max((int)((__double_as_longlong(a[e].x) >> 52) & 0x7ff),
+                         (int)((__double_as_longlong(a[e].y) >> 52) & 0x7ff)));
+        el = max(el, max((int)((__double_as_longlong(b[e].x) >> 52) & 0x7ff),
+                         (int)((__double_as_longlong(b[e].y) >> 52) & 0x7ff)));
+      }
+      Sp = 1083 - ep - kHead;
+      Sl = 1083 - el - kHead;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        P[e][0] = fx_in(a[e].x, 1085 - Sp);
+        P[e][1] = fx_in(a[e].y, 1085 - Sp);
+        L[e][0] = fx_in(b[e].x, 1085 - Sl);
+        L[e][1] = fx_in(b[e].y, 1085 - Sl);
+      }
+    }
+    int halved = 0;
+    for (int j = 0; j < count; ++j) {
+      const AdjRotFx &r = srot[j];
+      const int sig = __popcll(rep & r.z) & 1;
+      const int64_t gi = adj_dispatch_fx(r.uk, P, L, r, sig);
+      // gi is in units of 2^-(Sp + Sl - 2 halved - 62)
+      sacc[j][threadIdx.x] += fx_out(gi, 1086 - (Sp + Sl - 2 * halved - 62));
+      for (int h = r.halve; h > 0; --h) {
+        ++halved;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          P[e][0] >>= 1;
+          P[e][1] >>= 1;
+          L[e][0] >>= 1;
+          L[e][1] >>= 1;
+        }
+      }
+    }
+    const int ebp = 1086 - (Sp - halved), ebl = 1086 - (Sl - halved);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      phi[rep ^ run.soff[e]] = make_double2(sc * fx_out(P[e][0] + bias, ebp), sc * fx_out(P[e][1] + bias, ebp));
+      lam[rep ^ run.soff[e]] = make_double2(sc * fx_out(L[e][0] + bias, ebl), sc * fx_out(L[e][1] + bias, ebl));
+    }
+  }
+  __syncthreads();
+  // block sums in a fixed order: warp w reduces rows w, w + 8, ...
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = w; j < count; j += (int)(blockDim.x >> 5)) {
+    double v = 0.0;
+    for (int i = lane; i < (int)blockDim.x; i += 32) v += sacc[j][i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) partials[(size_t)run.rot[j].row * row_stride + blockIdx.x] = v;
+  }
+}
+
 __global__ void k_sum_rows(const double *__restrict__ partials, int n_blocks, double *__restrict__ out) {
   const double *p = partials + (size_t)blockIdx.x * n_blocks;
   double a = 0.0;
@@ -365,7 +621,21 @@ int run_blocks_t(int n) {
   return (int)(need < (uint64_t)cap ? (need ? need : 1) : cap);
 }
 
-int run_blocks(const sv_state *sv) { return sv->dtype == SV_C128 ? run_blocks_t<double>(sv->n) : run_blocks_t<float>(sv->n); }
+int run_blocks_fx(int n) {
+  // computed once, on first use (thread-safe static initialisation)
+  static const int cap = [] {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_run_fx, kThreads, 0) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    return (per_sm > 0 ? per_sm : 1) * device_sm_count();
+  }();
+  const uint64_t need = (((1ULL << n) >> kAdjD) + kThreads - 1) / kThreads;
+  return (int)(need < (uint64_t)cap ? (need ? need : 1) : cap);
+}
+
+int run_blocks(const sv_state *sv) { return sv->dtype == SV_C128 ? run_blocks_fx(sv->n) : run_blocks_t<float>(sv->n); }
 
 // The backward sweep as fused runs: rotations in applied order L-1 .. 0, grouped
 // greedily into runs of <= kAdjRun whose x-masks span <= kAdjD dimensions.
@@ -400,6 +670,23 @@ int adjoint_runs(sv_state *phi, sv_state *lam, const sv_plan *plan, const Pauli 
       piv[pos] = pv;
       ++d;
     };
+    // complex128 runs hold rotations with |beta| <= pi/2 only (tan(beta/2) <= 1,
+    // which the fixed-point run needs; only rotations of diagonal phase-sum
+    // stretches keep larger angles in the plan): a larger one takes a pass of
+    // its own in FP64 between runs, with the states at their plain scale
+    auto wide = [&](size_t k) {
+      return phi->dtype == SV_C128 && plan->sigma[k] != 0 && std::fabs(plan->beta[k]) > kHalfPi;
+    };
+    if (wide(i - 1)) {
+      const size_t k = i - 1;
+      const int s0 = anticommute(plan->ox[k], plan->oz[k], q0.x, q0.z) ? -1 : 1;
+      const int rc = adjoint_step(phi, lam, plan->ox[k], plan->oz[k], s0 * plan->beta[k],
+                                  phi->d_partials + (size_t)blocks * k, blocks);
+      if (rc) return rc;
+      gscale[k] = 1.0;
+      --i;
+      continue;
+    }
     std::vector<size_t> members;
     while (i > 0 && members.size() < (size_t)kAdjRun) {
       const size_t k = i - 1;
@@ -407,6 +694,7 @@ int adjoint_runs(sv_state *phi, sv_state *lam, const sv_plan *plan, const Pauli 
         --i;
         continue;
       }
+      if (wide(k)) break;
       const uint64_t rr = reduce(plan->ox[k]);
       if (rr != 0) {
         if (d >= kAdjD) break;
@@ -455,8 +743,8 @@ int adjoint_runs(sv_state *phi, sv_state *lam, const sv_plan *plan, const Pauli 
     run.scale = cprod;
     const int tr = trace_begin(phi, KN_ADJOINT_RUN);
     if (phi->dtype == SV_C128)
-      k_adjoint_run<double><<<blocks, kThreads, 0, phi->stream>>>((double2 *)phi->amps, (double2 *)lam->amps,
-                                                                  n_cosets, run, blocks, phi->d_partials);
+      k_adjoint_run_fx<<<blocks, kThreads, 0, phi->stream>>>((double2 *)phi->amps, (double2 *)lam->amps, n_cosets,
+                                                             run, blocks, phi->d_partials);
     else
       k_adjoint_run<float><<<blocks, kThreads, 0, phi->stream>>>((float2 *)phi->amps, (float2 *)lam->amps,
                                                                  n_cosets, run, blocks, phi->d_partials);
@@ -468,8 +756,10 @@ int adjoint_runs(sv_state *phi, sv_state *lam, const sv_plan *plan, const Pauli 
 
 }  // namespace
 
-int adjoint_step(sv_state *phi, sv_state *lam, uint64_t x, uint64_t z, double beta, double *d_out) {
-  const int blocks = step_blocks(phi->n);
+int adjoint_step(sv_state *phi, sv_state *lam, uint64_t x, uint64_t z, double beta, double *d_out,
+                 int max_blocks) {
+  int blocks = step_blocks(phi->n);
+  if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
   const double c = std::cos(0.5 * beta), s = std::sin(0.5 * beta);
   const uint64_t n_amps = 1ULL << phi->n;
   const int tr = trace_begin(phi, KN_ADJOINT);

@@ -257,5 +257,7 @@ int expval_impl(sv_state *sv, const uint64_t *x, const uint64_t *z, const double
 int pauli_sum_impl(sv_state *dst, sv_state *src, const uint64_t *x, const uint64_t *z,
                    const double *c, size_t count);
 // adjoint one-rotation step (adjoint.cu)
-int adjoint_step(sv_state *phi, sv_state *lam, uint64_t x, uint64_t z, double beta, double *d_out);
+// max_blocks > 0 caps the grid (the partial sums it writes per block)
+int adjoint_step(sv_state *phi, sv_state *lam, uint64_t x, uint64_t z, double beta, double *d_out,
+                 int max_blocks = 0);
 }  // namespace pr
