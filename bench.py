@@ -89,7 +89,7 @@ def peaks() -> dict:
 # source files that define each traced kernel family, per precision: a stored
 # ncu traffic figure counts only while these are unchanged since the capture
 KERNEL_SOURCES = {("k_coset", "c64"): ("kernels.cuh", "rotate.cu"),
-                  ("k_coset", "c128"): ("coset_fx.cuh", "kernels.cuh", "rotate.cu"),
+                  ("k_coset", "c128"): ("coset_fx.cuh", "fixed64.cuh", "kernels.cuh", "rotate.cu"),
                   ("k_diag_sum", "c64"): ("kernels.cuh", "rotate.cu"),
                   ("k_diag_sum", "c128"): ("kernels.cuh", "rotate.cu"),
                   ("k_expval", "c64"): ("reduce.cu",), ("k_expval", "c128"): ("reduce.cu",)}
