@@ -290,7 +290,13 @@ int trotter_expand(const uint64_t *x, const uint64_t *z, const double *c, size_t
  * "Extraction of Expectation Values", Eqs. Fmap and chfsexp).
  * out_norm2 (nullable) = <psi|psi>.  Terms are grouped by x-mask and several
  * groups are evaluated per pass; partial sums are reduced in a fixed order,
- * so repeated calls give bitwise-equal results. */
+ * so repeated calls give bitwise-equal results.  Arithmetic (n >= 4): every
+ * per-term sum is an exact 64-bit integer sum on a grid 2^-S chosen from the
+ * state's norm (S = 60 - ceil(log2 <psi|psi>)); complex64 products are exact
+ * and rounded once onto the grid, complex128 products are 62-bit fixed-point
+ * products on one exponent per 16 amplitudes, rounded once per transform
+ * entry.  n < 4: FP64 products and sums.  SV_EUNSUPPORTED if the norm is not
+ * finite (complex64: also if it exceeds about 2^52). */
 int expval_pauli_sum(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *coeff,
                      size_t count, double *out_energy, double *out_norm2);
 

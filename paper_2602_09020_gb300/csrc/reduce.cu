@@ -19,6 +19,7 @@
 #include <mutex>
 #include <cmath>
 
+#include "fixed64.cuh"
 #include "internal.h"
 
 namespace pr {
@@ -930,6 +931,173 @@ __global__ void __launch_bounds__(kWThreads, 4)
   }
 }
 
+// ---- complex128 <H> on the same plan, in 64-bit fixed point -------------------
+//
+// The tiles, groups, transforms and per-term integer sums of k_expval_fix, for
+// FP64 amplitudes: a tile's 32 components become signed integers below 2^59 on
+// one exponent per tile (fixed64.cuh; resolution 2^-57 of the tile's largest
+// component or finer), each pair product is a truncated 62-bit fixed-point
+// product (three 32 x 32 -> 64-bit multiplies), the group's 8 (16) pair values
+// go through the int64 Walsh-Hadamard transform, and every transform entry is
+// rounded once onto the grid 2^-S shared by all tiles, after which all sums are
+// exact.  A transform entry is at most the tile's squared norm, so with
+// S = 60 - ceil(log2 <a|a>) no sum exceeds 2^60.  No FP64 arithmetic per
+// amplitude: GB300's FP64 pipe bounded the FP64 version.
+
+// round(v 2^-k) for k > 0 (ties up; |v| < 2^61, so k >= 62 gives 0), v 2^-k for
+// k <= 0 (the choice of S keeps the result below 2^60)
+__device__ __forceinline__ long long fx_regrid(long long v, int k) {
+  if (k <= 0) return v << min(-k, 63);
+  const int kk = min(k, 62);
+  return (v + (1LL << (kk - 1))) >> kk;
+}
+
+template <int U>
+__device__ __forceinline__ void fx128_group(const long long (&re)[kWE], const long long (&im)[kWE], int imag, int k,
+                                            long long (*sw)[kWThreads]) {
+  long long W[kWE];
+  if (U == 0) {
+#pragma unroll
+    for (int l = 0; l < kWE; ++l) {
+      int32_t rh, rl, ih, il;
+      fx_limbs(re[l], rh, rl);
+      fx_limbs(im[l], ih, il);
+      W[l] = fx_prod(re[l], rh, rl) + fx_prod(im[l], ih, il);
+    }
+    fix_wht<kWE>(W);
+#pragma unroll
+    for (int l = 0; l < kWE; ++l) sw[l][threadIdx.x] = fx_regrid(W[l], k);
+  } else {
+    constexpr int H = fix_high_bit(U), P = kWE / 2;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int l = fix_leader(p, H), m = l ^ U;
+      int32_t mxh, mxl, myh, myl;
+      fx_limbs(re[m], mxh, mxl);
+      fx_limbs(im[m], myh, myl);
+      W[p] = !imag ? fx_prod(re[l], mxh, mxl) + fx_prod(im[l], myh, myl)    // Re conj(a_l) a_m
+                   : fx_prod(re[l], myh, myl) - fx_prod(im[l], mxh, mxl);   // Im conj(a_l) a_m
+    }
+    fix_wht<P>(W);
+#pragma unroll
+    for (int p = 0; p < P; ++p) sw[p][threadIdx.x] = fx_regrid(W[p], k);
+  }
+}
+
+__device__ __forceinline__ void fx128_dispatch(int u, int imag, const long long (&re)[kWE], const long long (&im)[kWE],
+                                               int k, long long (*sw)[kWThreads]) {
+  switch (u) {
+    case 0: fx128_group<0>(re, im, imag, k, sw); break;
+    case 1: fx128_group<1>(re, im, imag, k, sw); break;
+    case 2: fx128_group<2>(re, im, imag, k, sw); break;
+    case 3: fx128_group<3>(re, im, imag, k, sw); break;
+    case 4: fx128_group<4>(re, im, imag, k, sw); break;
+    case 5: fx128_group<5>(re, im, imag, k, sw); break;
+    case 6: fx128_group<6>(re, im, imag, k, sw); break;
+    case 7: fx128_group<7>(re, im, imag, k, sw); break;
+    case 8: fx128_group<8>(re, im, imag, k, sw); break;
+    case 9: fx128_group<9>(re, im, imag, k, sw); break;
+    case 10: fx128_group<10>(re, im, imag, k, sw); break;
+    case 11: fx128_group<11>(re, im, imag, k, sw); break;
+    case 12: fx128_group<12>(re, im, imag, k, sw); break;
+    case 13: fx128_group<13>(re, im, imag, k, sw); break;
+    case 14: fx128_group<14>(re, im, imag, k, sw); break;
+    case 15: fx128_group<15>(re, im, imag, k, sw); break;
+    default: break;
+  }
+}
+
+// S: the global grid exponent (units of 2^-S)
+template <typename Idx>
+__global__ void __launch_bounds__(kWThreads, 4)
+    k_expval_fx128(const double2 *__restrict__ amp, Idx n_tiles, const WhtRunDev run,
+                   const WhtGroupDev *__restrict__ ggroups, const WhtTermDev *__restrict__ gterms, int S,
+                   long long *__restrict__ partials, int reverse) {
+  __shared__ WhtGroupDev groups[kWGroups];
+  __shared__ Idx tz[kWTerms];
+  __shared__ int tslot[kWTerms];
+  __shared__ Idx soff[kWE];
+  __shared__ long long sw[kWE][kWThreads];
+  __shared__ long long sacc[kWTerms][kWThreads];
+  const int ng = run.ngroups, nt = run.nterms;
+  if (threadIdx.x < ng) groups[threadIdx.x] = ggroups[threadIdx.x];
+  if (threadIdx.x < nt) {
+    tz[threadIdx.x] = (Idx)gterms[threadIdx.x].z;
+    tslot[threadIdx.x] = gterms[threadIdx.x].slot;
+  }
+  if (threadIdx.x < kWE) {
+    uint64_t so = 0;
+    for (int b = 0; b < kWD; ++b)
+      if ((threadIdx.x >> b) & 1) so ^= run.basis[b];
+    soff[threadIdx.x] = (Idx)so;
+  }
+  for (int j = 0; j < kWTerms; ++j) sacc[j][threadIdx.x] = 0;
+  __syncthreads();
+  const Idx stride = (Idx)gridDim.x * blockDim.x;
+  for (Idx c = (Idx)blockIdx.x * blockDim.x + threadIdx.x; c < n_tiles; c += stride) {
+    Idx rep = reverse ? n_tiles - 1 - c : c;
+#pragma unroll
+    for (int b = 0; b < kWD; ++b) {
+      const int pv = run.piv[b];
+      rep = ((rep >> pv) << (pv + 1)) | (rep & ((Idx(1) << pv) - 1));
+    }
+    long long re[kWE], im[kWE];
+    int k;  // transform entries are in units of 2^-(2 St - 62); to the grid 2^-S
+    {
+      double2 a[kWE];
+      int emax = 0;
+#pragma unroll
+      for (int l = 0; l < kWE; ++l) {
+        a[l] = amp[rep ^ soff[l]];
+        emax = max(emax, max((int)((__double_as_longlong(a[l].x) >> 52) & 0x7ff),
+                             (int)((__double_as_longlong(a[l].y) >> 52) & 0x7ff)));
+      }
+      const int St = 1081 - emax;  // |a| < 2^(emax - 1022): every component below 2^59
+#pragma unroll
+      for (int l = 0; l < kWE; ++l) {
+        re[l] = fx_in(a[l].x, 1085 - St);
+        im[l] = fx_in(a[l].y, 1085 - St);
+      }
+      k = 2 * St - 62 - S;
+    }
+    for (int g = 0; g < ng; ++g) {
+      const WhtGroupDev G = groups[g];
+#pragma unroll
+      for (int l = 0; l < kWE; ++l) asm volatile("" : "+l"(re[l]), "+l"(im[l]));
+      fx128_dispatch(G.u, G.imag, re, im, k, sw);
+      for (int t = G.t0; t < G.t1; ++t) {
+        const long long v = sw[tslot[t]][threadIdx.x];
+        const long long s = -(long long)(__popcll((unsigned long long)(rep & tz[t])) & 1);
+        sacc[t][threadIdx.x] += (v ^ s) - s;
+      }
+    }
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = w; j < kWTerms; j += (int)(blockDim.x >> 5)) {
+    long long v = 0;
+    for (int i = lane; i < (int)blockDim.x; i += 32) v += sacc[j][i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) partials[(size_t)blockIdx.x * kWTerms + j] = v;
+  }
+}
+
+// <a|a> of a complex128 state in FP64, per block (only used to pick S)
+__global__ void __launch_bounds__(kThreads) k_norm_est128(const double2 *__restrict__ amp, uint64_t n, double *out) {
+  double acc = 0.0, unused = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double2 v = amp[i];
+    acc = fma(v.x, v.x, fma(v.y, v.y, acc));
+  }
+  block_sum2(acc, unused);
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = acc;
+    out[2 * blockIdx.x + 1] = acc;
+  }
+}
+
 // results[r][j] = sum over blocks of partials[r][b][j]; one CTA per run
 __global__ void k_finish_fix(const long long *__restrict__ partials, int n_blocks, long long *__restrict__ results) {
   __shared__ long long red[kThreads / 32];
@@ -1131,16 +1299,24 @@ void plan_fix(const sv_state *sv, const uint64_t *x, const uint64_t *z, const do
   }
 }
 
+template <typename K>
+int fix_cap(K kernel) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return (per_sm > 0 ? per_sm : 1) * device_sm_count();
+}
+
+// complex64 (k_expval_fix, exact products of FP32 components) or complex128
+// (k_expval_fx128, 62-bit fixed-point products) on the same plan
 template <typename Idx>
 int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *energy, double *norm2) {
-  static const int cap = [] {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expval_fix<Idx>, kWThreads, 0) != cudaSuccess) {
-      cudaGetLastError();
-      per_sm = 1;
-    }
-    return (per_sm > 0 ? per_sm : 1) * device_sm_count();
-  }();
+  static const int cap64 = fix_cap(k_expval_fix<Idx>);
+  static const int cap128 = fix_cap(k_expval_fx128<Idx>);
+  const bool c128 = sv->dtype == SV_C128;
+  const int cap = c128 ? cap128 : cap64;
   const uint64_t n_amps = 1ULL << sv->n;
   const uint64_t n_tiles = n_amps >> kWD;
   const uint64_t need = (n_tiles + kWThreads - 1) / kWThreads;
@@ -1172,9 +1348,12 @@ int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *ener
   double *d_est = sv->d_results + kWTerms * runs.size();
   {
     const int tr = trace_begin(sv, KN_EXPVAL);
-    k_norm_est<<<est_blocks, kThreads, 0, sv->stream>>>((const float2 *)sv->amps, n_amps, d_est);
+    if (c128)
+      k_norm_est128<<<est_blocks, kThreads, 0, sv->stream>>>((const double2 *)sv->amps, n_amps, d_est);
+    else
+      k_norm_est<<<est_blocks, kThreads, 0, sv->stream>>>((const float2 *)sv->amps, n_amps, d_est);
     PR_CHECK_LAUNCH();
-    trace_end(sv, tr, KN_EXPVAL, 8.0 * (double)n_amps);
+    trace_end(sv, tr, KN_EXPVAL, (c128 ? 16.0 : 8.0) * (double)n_amps);
   }
   PR_CUDA(cudaMemcpyAsync(sv->h_results, d_est, 2 * est_blocks * sizeof(double), cudaMemcpyDeviceToHost, sv->stream));
   PR_CUDA(cudaStreamSynchronize(sv->stream));
@@ -1183,7 +1362,7 @@ int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *ener
     plain += sv->h_results[2 * i];
     scaled += sv->h_results[2 * i + 1];
   }
-  if (!std::isfinite(plain)) return fail(SV_EUNSUPPORTED, "state norm is not finite in FP32");
+  if (!std::isfinite(plain)) return fail(SV_EUNSUPPORTED, "state norm is not finite");
   const double nest = std::isfinite(scaled) ? scaled : plain;
   // S = 60 - ceil(log2 <a|a>) (estimate widened by 2 %): every per-term sum,
   // and every intermediate of the tile transforms, is bounded by
@@ -1192,19 +1371,27 @@ int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *ener
   // n <= 32).  The scaled sum loses squares below 2^-254, at most 2^(n-254) of
   // mass, under 0.8 % of any estimate above 2^(n-247), which therefore bounds
   // S; the unscaled sum is used only when it is at least about 1.
-  const double est = std::max(nest, std::ldexp(1.0, sv->n - 247));
+  // For complex128 the FP64 squares lose only amplitudes below 2^-537, at most
+  // 2^(n-1074) of mass, so the floor is 2^(n-1000).
+  const double est = std::max(nest, std::ldexp(1.0, sv->n - (c128 ? 1000 : 247)));
   const int S = 60 - (int)std::ceil(std::log2(est * 1.02));
-  if (S < 8) return fail(SV_EUNSUPPORTED, "state norm %g too large for the fixed-point sums", nest);
+  // complex128 takes any finite norm (S >= -1024); complex64 transforms need S >= 8
+  if (!c128 && S < 8) return fail(SV_EUNSUPPORTED, "state norm %g too large for the fixed-point sums", nest);
   long long *part = (long long *)sv->d_partials;
   long long *res = (long long *)sv->d_results;
   for (size_t r = 0; r < runs.size(); ++r) {
     const char *base = (const char *)sv->d_stage + off[r];
     const int tr = trace_begin(sv, KN_EXPVAL);
-    k_expval_fix<Idx><<<blocks, kWThreads, 0, sv->stream>>>(
-        (const float2 *)sv->amps, (Idx)n_tiles, runs[r].dev, (const WhtGroupDev *)base,
-        (const WhtTermDev *)(base + kGroupBytes), 14 - S, part + (size_t)kWTerms * blocks * r, (int)((r + 1) & 1));
+    if (c128)
+      k_expval_fx128<Idx><<<blocks, kWThreads, 0, sv->stream>>>(
+          (const double2 *)sv->amps, (Idx)n_tiles, runs[r].dev, (const WhtGroupDev *)base,
+          (const WhtTermDev *)(base + kGroupBytes), S, part + (size_t)kWTerms * blocks * r, (int)((r + 1) & 1));
+    else
+      k_expval_fix<Idx><<<blocks, kWThreads, 0, sv->stream>>>(
+          (const float2 *)sv->amps, (Idx)n_tiles, runs[r].dev, (const WhtGroupDev *)base,
+          (const WhtTermDev *)(base + kGroupBytes), 14 - S, part + (size_t)kWTerms * blocks * r, (int)((r + 1) & 1));
     PR_CHECK_LAUNCH();
-    trace_end(sv, tr, KN_EXPVAL, 8.0 * (double)n_amps);
+    trace_end(sv, tr, KN_EXPVAL, (c128 ? 16.0 : 8.0) * (double)n_amps);
   }
   {
     const int tr = trace_begin(sv, KN_FINISH);
@@ -1231,7 +1418,7 @@ int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *ener
 
 int expval_impl(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c, size_t count,
                 double *energy, double *norm2) {
-  if (sv->dtype == SV_C64 && sv->n >= kWD) {
+  if (sv->n >= kWD) {
     if (count && (!x || !z || !c)) return fail(SV_EINVAL, "NULL term arrays");
     int rc = validate_masks(sv->n, x, z, count);
     if (rc) return rc;

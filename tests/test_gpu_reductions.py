@@ -74,17 +74,19 @@ def test_apply_pauli_sum(orc, dtype):
     assert np.max(np.abs(got - want)) < tol * max(1.0, np.abs(ham.c).sum() / 10)
 
 
-@pytest.mark.parametrize("scale", [1.0, 1.5, 1e-3, 1e-20])
-def test_expval_c64_group_structure(orc, scale):
-    """c64 <H> with x-masks that are XOR combinations of one another (so a run
+@pytest.mark.parametrize("dtype,scale", [("c64", 1.0), ("c64", 1.5), ("c64", 1e-3), ("c64", 1e-20),
+                                         ("c128", 1.0), ("c128", 1e-3), ("c128", 1e-150), ("c128", 1e120)])
+def test_expval_group_structure(orc, dtype, scale):
+    """<H> with x-masks that are XOR combinations of one another (so a run
     holds x-masks whose coordinates in the run basis are 3, 5, 6, 7, ...), both
     Re and Im parts, one x-mask with 40 terms (more than one run holds), 70
-    diagonal terms and identities spread over several runs, at four state
+    diagonal terms and identities spread over several runs, at several state
     norms.  The fixed-point grid 2^-S follows the norm (S = 60 - ceil(log2
-    <a|a>), bounded where the norm is too small for an FP32 estimate), and each
-    sum is exact up to 2^-(S+1) per product: the result matches the oracle on
-    the same rounded amplitudes to FP64 accuracy relative to the norm, and
-    repeated calls agree bitwise."""
+    <a|a>), bounded where the norm is too small for the estimate), and each
+    sum is exact up to 2^-(S+1) per transform entry (complex64: exact products;
+    complex128: 62-bit fixed-point products on one exponent per 16-amplitude
+    tile): the result matches the oracle on the same rounded amplitudes to
+    FP64 accuracy relative to the norm, and repeated calls agree bitwise."""
     n = 11
     rng = np.random.default_rng(17)
     psi = synth.random_state(n, 31) * scale
@@ -113,13 +115,13 @@ def test_expval_c64_group_structure(orc, scale):
     x = np.array(x, dtype=np.uint64)
     z = np.array(z, dtype=np.uint64)
     c = rng.normal(size=len(x))
-    psi32 = psi.astype(np.complex64)
-    ref = orc.expval(psi32.astype(np.complex128), n, x, z, c)
-    sv = upload(n, "c64", psi)
+    psi_r = psi.astype(np.complex64).astype(np.complex128) if dtype == "c64" else psi
+    ref = orc.expval(psi_r, n, x, z, c)
+    sv = upload(n, dtype, psi)
     e1, nrm1 = capi.expval_pauli_sum(sv, x, z, c)
     e2, nrm2 = capi.expval_pauli_sum(sv, x, z, c)
     capi.sv_free(sv)
-    norm = float(np.vdot(psi32.astype(np.complex128), psi32.astype(np.complex128)).real)
-    assert abs(e1 - ref) < 1e-12 * max(1.0, np.abs(c).sum()) * norm, (e1, ref)
+    norm = float(np.vdot(psi_r, psi_r).real)
+    assert abs(e1 - ref) < 1e-12 * np.abs(c).sum() * norm, (e1, ref)
     assert abs(nrm1 - norm) <= 1e-13 * norm
     assert e1 == e2 and nrm1 == nrm2
