@@ -89,6 +89,7 @@ def peaks() -> dict:
 # source files that define each traced kernel family, per precision: a stored
 # ncu traffic figure counts only while these are unchanged since the capture
 KERNEL_SOURCES = {("k_coset", "c64"): ("kernels.cuh", "rotate.cu"),
+                  ("k_chain2", "c64"): ("chain.cu", "kernels.cuh", "internal.h"),
                   ("k_coset", "c128"): ("coset_fx.cuh", "fixed64.cuh", "kernels.cuh", "rotate.cu"),
                   ("k_diag_sum", "c64"): ("kernels.cuh", "rotate.cu"),
                   ("k_diag_sum", "c128"): ("kernels.cuh", "rotate.cu"),
@@ -290,6 +291,7 @@ def run_ours(a):
         plan = capi.plan_create(a.n, dtype, rx, rz, rt, a.fusion_depth, sh)
         plan_ms = 1000.0 * (time.perf_counter() - t0)
         nrot, nruns, ndiag = capi.plan_stats(plan)
+        nsweeps = capi.plan_sweeps(plan)
         dmax = a.fusion_depth if a.fusion_depth >= 0 else capi.plan_tuned_depth(a.n, dtype)[0]
         sv = capi.sv_alloc(a.n, dtype, sh)
         out = {}
@@ -318,7 +320,7 @@ def run_ours(a):
         ms = [e0.elapsed_time(e1) for e0, e1 in ev]
         capi.sv_free(sv)
         capi.plan_free(plan)
-        return {"ms": ms, "plan_ms": plan_ms, "runs": nruns, "dmax": dmax, "diag_runs": ndiag, "nrot": nrot,
+        return {"ms": ms, "plan_ms": plan_ms, "runs": nruns, "sweeps": nsweeps, "dmax": dmax, "diag_runs": ndiag, "nrot": nrot,
                 "trace": rows, "clocks": ck, "energy": out["energy"], "norm2": out["norm2"]}
 
     def roofline(rows: dict, steps: int, dtype: str):
@@ -337,6 +339,22 @@ def run_ours(a):
         achieved = by / (tot_ms / 1000.0) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "peak_source": pk["source"]}
+        if name.startswith("k_chain"):
+            # a chained pass applies two runs per sweep of the state and is bound
+            # by the FP32 FMA pipe (the pair updates: 4 flops per amplitude and
+            # rotation), not by HBM; its HBM figures stay beside the roofline
+            tflops = fl / (tot_ms / 1000.0) / 1e12
+            if fp32_peak.get("tflops"):
+                peak, src = fp32_peak["tflops"], fp32_peak["source"]
+            else:
+                sms = torch.cuda.get_device_properties(0).multi_processor_count
+                peak = sms * 128 * 2 * 2.070e9 / 1e12
+                src = f"nominal: {sms} SMs x 128 FP32 FMA per clock x 2 flops x 2070 MHz"
+            roof = {"bound": "alu", "pipe": "fp32_fma", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                    "frac": tflops / peak, "peak_source": src,
+                    "hbm": {"achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                            "frac": achieved / pk["hbm_gbs"], "peak_source": pk["source"]},
+                    "runs_per_sweep": 2}
         if dtype == "c128" and name.startswith("k_coset"):
             # the complex128 pass runs its products on the integer pipes: per
             # amplitude and rotation two 62-bit fixed-point products of three
@@ -353,11 +371,12 @@ def run_ours(a):
 
     # measured arithmetic peaks (FP64 FMA, wide integer multiply-add), taken
     # before the timed steps so the complex128 roofline can use them
-    int_peak = {}
+    int_peak, fp32_peak = {}, {}
     arith = None
     if not a.skip_extras:
         arith = probe_peaks(capi, torch)
         int_peak = {"tops": arith["int_mul_wide_tops"], "source": "measured (probe kernel, this run)"}
+        fp32_peak = {"tflops": arith["fp32_tflops"], "source": "measured (packed FP32x2 FMA probe kernel, this run)"}
 
     # the fusion depth plan_create(-1) takes comes from the library's autotuner,
     # run on the first Trotter step of the list for each precision (untimed
@@ -402,7 +421,7 @@ def run_ours(a):
         o = measure(other, max(1, min(a.steps, 2)), 1, "blocks")
         o_roof, _ = roofline(o["trace"], max(1, min(a.steps, 2)), other)
         extras[other] = {"value": R / (statistics.mean(o["ms"]) / 1000.0), "ms_per_step": statistics.mean(o["ms"]),
-                         "passes_per_step": o["runs"], "fusion_depth": o["dmax"], "energy": o["energy"], "roofline": o_roof}
+                         "passes_per_step": o["sweeps"], "runs_per_step": o["runs"], "fusion_depth": o["dmax"], "energy": o["energy"], "roofline": o_roof}
         # gate-decomposed path on the same GPU, same dtype: a strided sample of one Trotter step
         sample = slice(0, a.terms, 4)
         gx, gz, gt = rx[sample], rz[sample], rt[sample]
@@ -488,7 +507,7 @@ def run_ours(a):
 
     if rank != 0:
         return 0
-    passes = main["runs"]
+    passes = main["sweeps"]
     line = {
         "metric": METRIC, "value": value, "unit": "rotations/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -501,7 +520,7 @@ def run_ours(a):
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": main["clocks"],
-        "passes_per_step": passes, "diag_passes_per_step": main["diag_runs"],
+        "passes_per_step": passes, "runs_per_step": main["runs"], "diag_passes_per_step": main["diag_runs"],
         "rotations_per_pass": main["nrot"] / max(1, passes),
         "effective_gbs": R * sweep_bytes / (ms_step / 1000.0) / 1e9,
         "rescaled_runtime_s": (ms_step / 1000.0) / (R * (1 << a.n)),
@@ -570,10 +589,11 @@ def precision_report(capi, a, ham, rx, rz, rt, basis, sh):
 
 
 def probe_peaks(capi, torch, reps: int = 3) -> dict:
-    """Measured arithmetic peaks on this GPU: FP64 FMA and 32x32->64 integer
-    multiply-add rates from the library's probe kernels (grids of 8 CTAs per SM,
+    """Measured arithmetic peaks on this GPU: FP64 FMA, 32x32->64 integer
+    multiply-add and packed FP32x2 FMA rates from the library's probe kernels (grids of 8 CTAs per SM,
     CUDA events on the launching stream, best of `reps` launches), with the SM
-    clock sampled during the launches; ops x 2 for FLOP/s."""
+    clock sampled during the launches; ops x 2 for FLOP/s (x 4 for the packed
+    FP32x2 FMA)."""
     own = torch.cuda.Stream()
     sh = int(own.cuda_stream)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -582,7 +602,7 @@ def probe_peaks(capi, torch, reps: int = 3) -> dict:
     out = {"blocks": blocks, "threads_per_block": 256, "chains_per_thread": 8}
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
-    for kind, name, iters in ((0, "fp64_fma", 4000), (1, "int_mul_wide", 40000)):
+    for kind, name, iters in ((0, "fp64_fma", 4000), (1, "int_mul_wide", 40000), (2, "fp32x2_fma", 40000)):
         capi.sv_probe_rate(kind, blocks, 16, buf.data_ptr(), sh)  # warm
         best = None
         for _ in range(reps):
@@ -596,6 +616,7 @@ def probe_peaks(capi, torch, reps: int = 3) -> dict:
         out[name] = {"ops_per_s": ops / (best / 1000.0), "ms": best, "ops": ops}
     out["fp64_tflops"] = 2.0 * out["fp64_fma"]["ops_per_s"] / 1e12
     out["int_mul_wide_tops"] = out["int_mul_wide"]["ops_per_s"] / 1e12
+    out["fp32_tflops"] = 4.0 * out["fp32x2_fma"]["ops_per_s"] / 1e12
     out["clocks"] = clocks.stop()
     return out
 
@@ -625,7 +646,7 @@ def large_compare(capi, torch, barrier, n: int = 29, terms: int = 5000, seed: in
             e, nrm = capi.expval_pauli_sum(sv, ham.x, ham.z, ham.c)
             capi.sv_materialize(sv)
             barrier()
-            passes = capi.plan_stats(plan)[1]
+            passes = capi.plan_sweeps(plan)
         finally:
             capi.plan_free(plan)
             capi.sv_free(sv)
@@ -726,7 +747,7 @@ def locality_measure(capi, torch, n: int, dtype: str, barrier, terms: int = 100,
         e[3].record(own)
         barrier()
         fused_ms, gate_ms = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
-        passes = capi.plan_stats(plan)[1]
+        passes = capi.plan_sweeps(plan)
         capi.plan_free(plan)
         capi.sv_free(sv)
         rows.append({"L": L, "rotations": len(rt), "fused_ms": fused_ms, "fused_passes": passes,
@@ -826,12 +847,13 @@ def large_measure(capi, torch, barrier, n: int = 30, terms: int = 5000, seed: in
         e, nrm = capi.expval_pauli_sum(sv, ham.x, ham.z, ham.c)
         e2.record(own)
         barrier()
-        passes = capi.plan_stats(plan)[1]
+        passes = capi.plan_sweeps(plan)
+        runs = capi.plan_stats(plan)[1]
     finally:
         capi.sv_free(sv)
         capi.plan_free(plan)
     rot_ms, h_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
-    return {"n": n, "dtype": "c64", "terms": terms, "rotations": len(rt), "passes": passes,
+    return {"n": n, "dtype": "c64", "terms": terms, "rotations": len(rt), "passes": passes, "runs": runs,
             "rotations_ms": rot_ms, "expval_ms": h_ms, "rotations_per_s": len(rt) / (rot_ms / 1000.0),
             "hbm_fraction_algorithmic": passes * 2.0 * 8 * (1 << n) / (rot_ms / 1000.0) / 1e9 / peaks()["hbm_gbs"],
             "energy": e, "norm_drift": abs(nrm - 1.0)}

@@ -267,8 +267,19 @@ int plan_inspect(int n_qubits, int dtype, const uint64_t *x, const uint64_t *z, 
                  size_t *out_rotations);
 
 /* Plan statistics: number of rotations (after dropping identities), number
- * of fused runs (= HBM passes), of which diagonal phase-sum runs. */
+ * of fused runs, of which diagonal phase-sum runs.  Each run is one HBM pass
+ * unless plan_sweeps says fewer. */
 int plan_stats(const sv_plan *plan, size_t *n_rotations, size_t *n_runs, size_t *n_diag_runs);
+
+/* *n_sweeps = passes over the state that plan_apply launches.  A complex64
+ * plan with n >= 13 applies pairs of consecutive runs in one chained pass when
+ * their spans and index bits 0..3 fit in 12 dimensions (Sec. "Multi-qubit
+ * rotations in a fullstate simulator": each rotation pairs k with k ^ x inside
+ * a coset of its run's span, so a coset of the joint span is closed under both
+ * runs); then n_sweeps < n_runs.  Setting the environment variable
+ * PAULIROT_CHAIN=0 before plan_create turns chaining off (same results, bit for
+ * bit).  SV_EINVAL for a null argument. */
+int plan_sweeps(const sv_plan *plan, size_t *n_sweeps);
 
 /* ---- Trotter products (host) ----------------------------------------------------- */
 
@@ -444,7 +455,9 @@ int sv_trace_stop(sv_state *sv, sv_trace_row *rows, int cap, int *n_rows);
  * arithmetic pipe busy: `blocks` CTAs of 256 threads, each thread running eight
  * independent dependency chains of `iters` operations.  kind 0: FP64 fused
  * multiply-add; kind 1: 32 x 32 -> 64-bit signed integer multiply-add (the
- * operation the complex128 passes are built from).  The caller times the launch
+ * operation the complex128 passes are built from); kind 2: packed FP32x2 fused
+ * multiply-add (two FP32 FMAs per operation, the complex64 passes' update).
+ * The caller times the launch
  * with CUDA events; *out_ops (nullable) = operations the launch performs
  * (blocks * 256 * iters * 8).  dev_out: caller-owned device buffer of
  * blocks * 256 eight-byte values, overwritten with the chains' results.

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpaulirot.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 SOURCES = ["state.cu", "plan.cu", "rotate.cu", "reduce.cu", "adjoint.cu", "gates.cu", "batch.cu", "clifford.cu", "measure.cu",
-           "tune.cu", "checkpoint.cu", "trace.cu", "probe.cu", "shard.cu"]
+           "tune.cu", "checkpoint.cu", "trace.cu", "probe.cu", "shard.cu", "chain.cu"]
 
 
 def _nvcc() -> str:

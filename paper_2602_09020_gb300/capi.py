@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
         "plan_apply": ([vp, vp], i),
         "plan_free": ([vp], i),
         "plan_stats": ([vp, P(sz), P(sz), P(sz)], i),
+        "plan_sweeps": ([vp, P(sz)], i),
         "plan_inspect": ([i, i, vp, vp, vp, sz, i, vp, sz, P(sz), P(sz)], i),
         "plan_autotune": ([vp, vp, vp, vp, sz, i, i, P(i), vp], i),
         "plan_tuned_depth": ([i, i, P(i), P(i)], i),
@@ -132,7 +133,7 @@ def exported_symbols() -> Sequence[str]:
     return ["sv_last_error", "sv_version", "sv_alloc", "sv_wrap", "sv_free", "sv_set_stream",
             "sv_device_ptr", "sv_info", "sv_set_basis_state", "sv_from_host", "sv_to_host",
             "sv_materialize", "sv_copy", "sv_save", "sv_load", "frame_reset", "frame_apply_pauli", "frame_get",
-            "apply_pauli_rotations", "plan_create", "plan_apply", "plan_free", "plan_stats", "plan_inspect",
+            "apply_pauli_rotations", "plan_create", "plan_apply", "plan_free", "plan_stats", "plan_sweeps", "plan_inspect",
             "plan_autotune", "batch_autotune", "plan_tuned_depth", "plan_set_tuned_depth", "plan_tune_cache_load",
             "plan_tune_cache_save",
             "trotter_expand", "expval_pauli_sum", "expval_pauli_sum_noalloc", "apply_pauli_sum", "rotation_grads",
@@ -287,6 +288,14 @@ def plan_stats(plan: int) -> Tuple[int, int, int]:
     a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
     _check(lib().plan_stats(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def plan_sweeps(plan: int) -> int:
+    """Passes over the state that plan_apply launches (a chained pass applies
+    two runs)."""
+    v = ctypes.c_size_t()
+    _check(lib().plan_sweeps(plan, ctypes.byref(v)))
+    return v.value
 
 
 def plan_autotune(sv: int, x, z, angles, max_depth: int = 0, reps: int = 0) -> Tuple[int, np.ndarray]:
@@ -486,7 +495,8 @@ def sv_trace_stop(sv: int) -> dict:
 
 def sv_probe_rate(kind: int, blocks: int, iters: int, dev_out: int, stream: int = 0) -> float:
     """Launch one arithmetic-rate probe (kind 0: FP64 FMA, 1: 32x32->64 integer
-    multiply-add) on `stream`; returns the operations it performs."""
+    multiply-add, 2: packed FP32x2 FMA) on `stream`; returns the operations it
+    performs."""
     ops = ctypes.c_double()
     _check(lib().sv_probe_rate(int(kind), int(blocks), int(iters), ctypes.c_void_p(dev_out),
                                ctypes.c_void_p(stream), ctypes.byref(ops)))

@@ -123,6 +123,32 @@ struct RunDev {
   int32_t seg[(1 << kDiagClassBits) + 1];  // diag runs: rotation ranges per low-bit class
 };
 
+// Two consecutive complex64 coset runs applied in one HBM pass (chain.cu).  A
+// CTA owns a block of 2^kChainDim amplitudes: a coset of a subspace W that
+// contains both runs' spans and index bits 0..3.  Block coordinate i stands for
+// the index-space vector w[i] (w[i] = 2^i for i < 4, bits 0..3 clear above);
+// amplitude index = block base ^ (xor of w[i] over the set bits i).
+constexpr int kChainDim = 12;  // 2^12 amplitudes per block: 128 threads x 32 amplitudes
+struct ChainSubDev {
+  uint64_t off[16];   // element offsets (the run's basis padded to 4 vectors)
+  uint64_t padv[4];   // index-space vector of basis slot b >= d, else 0
+  uint16_t offc[16];  // the same offsets in block coordinates
+  int32_t pivc[4];    // pivots of the padded span in block coordinates, ascending
+  int32_t d, first, count, fold;
+  double fold_re, fold_im;
+};
+struct ChainDev {
+  uint64_t w[kChainDim];
+  int32_t wpiv[kChainDim];  // pivot bits of W, ascending (block bases have zeros there)
+  int32_t pad;
+  ChainSubDev sub[2];
+};
+// one launch of a plan: run `run` alone (chain < 0) or runs run, run + 1 as
+// the chained pass chains[chain]
+struct PlanStep {
+  int32_t run, chain;
+};
+
 // Expectation-value run: groups of terms whose x-masks lie in one span.
 struct ExpTermDev {
   uint64_t z;
@@ -163,7 +189,7 @@ struct TraceRec {
 enum KernelId {
   KN_COSET0 = 0, KN_COSET1, KN_COSET2, KN_COSET3, KN_COSET4, KN_COSET5,
   KN_DIAG_SUM, KN_EXPVAL, KN_FINISH, KN_PAULI_SUM, KN_MATERIALIZE, KN_SET_BASIS,
-  KN_ADJOINT, KN_SUM_ROWS, KN_GATE1, KN_DIAG1, KN_CNOT, KN_PROJECT, KN_ADJOINT_RUN, KN_COUNT
+  KN_ADJOINT, KN_SUM_ROWS, KN_GATE1, KN_DIAG1, KN_CNOT, KN_PROJECT, KN_ADJOINT_RUN, KN_CHAIN, KN_COUNT
 };
 }  // namespace pr
 
@@ -206,6 +232,9 @@ struct sv_state {
 struct sv_plan {
   int n = 0, dtype = SV_C128, dmax = 0;
   std::vector<pr::RunDev> runs;
+  // launch order of apply_plan; empty: one launch per run
+  std::vector<pr::PlanStep> steps;
+  std::vector<pr::ChainDev> chains;
   pr::RotDev *d_rots = nullptr;
   pr::DiagDev *d_diag = nullptr;
   size_t n_rots = 0, n_diag = 0;
@@ -236,6 +265,10 @@ int device_sm_count();
 
 // launch one run of a plan (rotate.cu)
 int launch_run(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t fx, uint64_t fz);
+// chained passes (chain.cu): pair up consecutive runs of a complex64 plan
+// (fills plan->steps and plan->chains), and launch one chained pass
+void build_chains(sv_plan *plan);
+int launch_chain(sv_state *sv, const sv_plan *plan, const ChainDev &chain, uint64_t fx, uint64_t fz);
 int prepare_tables(int dtype);
 int table_pointer(int dtype, const void **out);
 // basis state and in-place frame application (state.cu)

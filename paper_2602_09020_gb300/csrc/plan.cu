@@ -346,6 +346,7 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
   p->n_effective = items.size();
   p->n_rots = rots.size();
   p->n_diag = diags.size();
+  build_chains(p);
   if (!upload) return SV_OK;
 
   if (!diags.empty()) {
@@ -380,9 +381,17 @@ int apply_plan(sv_state *sv, sv_plan *plan) {
     return fail(SV_EINVAL, "plan built for n=%d dtype=%d, state has n=%d dtype=%d", plan->n, plan->dtype,
                 sv->n, sv->dtype);
   const Pauli q0 = sv->frame;
-  for (const RunDev &r : plan->runs) {
-    int rc = launch_run(sv, plan, r, q0.x, q0.z);
-    if (rc) return rc;
+  if (plan->steps.empty()) {
+    for (const RunDev &r : plan->runs) {
+      int rc = launch_run(sv, plan, r, q0.x, q0.z);
+      if (rc) return rc;
+    }
+  } else {
+    for (const PlanStep &st : plan->steps) {
+      int rc = st.chain >= 0 ? launch_chain(sv, plan, plan->chains[st.chain], q0.x, q0.z)
+                             : launch_run(sv, plan, plan->runs[st.run], q0.x, q0.z);
+      if (rc) return rc;
+    }
   }
   // Q <- Q0 Qp (-1)^{<Qp, Q0>}: the frame factors picked up the runtime signs
   Pauli f = pauli_mul(q0, plan->frame);
@@ -453,6 +462,12 @@ int plan_stats(const sv_plan *plan, size_t *n_rotations, size_t *n_runs, size_t 
   if (n_rotations) *n_rotations = plan->n_effective;
   if (n_runs) *n_runs = plan->runs.size();
   if (n_diag_runs) *n_diag_runs = plan->n_diag_runs;
+  return SV_OK;
+}
+
+int plan_sweeps(const sv_plan *plan, size_t *n_sweeps) {
+  if (!plan || !n_sweeps) return fail(SV_EINVAL, "NULL argument");
+  *n_sweeps = plan->steps.empty() ? plan->runs.size() : plan->steps.size();
   return SV_OK;
 }
 

@@ -11,7 +11,7 @@ namespace pr {
 static const char *kNames[KN_COUNT] = {
     "k_coset_d0", "k_coset_d1", "k_coset_d2", "k_coset_d3", "k_coset_d4", "k_coset_d5",
     "k_diag_sum", "k_expval", "k_finish", "k_pauli_sum", "k_materialize", "k_set_one",
-    "k_adjoint_step", "k_sum_rows", "k_hadamard", "k_diag1", "k_cnot", "k_project", "k_adjoint_run"};
+    "k_adjoint_step", "k_sum_rows", "k_hadamard", "k_diag1", "k_cnot", "k_project", "k_adjoint_run", "k_chain2"};
 
 static int next_event(sv_state *sv) {
   if (sv->events_used == (int)sv->events.size()) {

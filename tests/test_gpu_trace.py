@@ -51,6 +51,7 @@ def test_block_trace_counts_match_launch_trace(dtype):
         assert per_launch[k][2] == pytest.approx(per_block[k][2])  # bytes
         assert per_block[k][1] > 0
     rot_launches = sum(v[0] for k, v in per_block.items() if k.startswith(("k_coset", "k_diag_sum")))
+    rot_launches += 2 * per_block.get("k_chain2", (0,))[0]  # a chained pass applies two runs
     assert rot_launches == n_runs
     # the blocks of one plan application tile the region between the two events
     total = sum(v[1] for v in rows.values())
