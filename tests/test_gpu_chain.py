@@ -7,7 +7,7 @@ values.  Cases: the Jordan-Wigner workload's shape, random strings whose
 x-masks touch bit 0 and bits 0..3 (which the block layout treats specially),
 runs of dimension below 4 (padded to 4 inside the chain), diagonal rotations
 inside runs, angles beyond pi/2 (frame factors), a running-scale fold, a Pauli
-frame set before the plan is applied, and n = 14 (two blocks), 15 and 17.
+frame set before the plan is applied, and n = 13 (two blocks of 2^12) to 17.
 """
 import os
 
@@ -71,7 +71,7 @@ def low_bit_paulis(n, count, seed):
 
 CASES = [
     # (name, n, depth)
-    ("jw", 14, 4), ("jw", 15, 4), ("jw", 17, 4), ("jw", 15, 3), ("jw", 15, 2),
+    ("jw", 13, 4), ("jw", 14, 4), ("jw", 15, 4), ("jw", 17, 4), ("jw", 15, 3), ("jw", 15, 2),
     ("span6", 14, 4), ("span6", 16, 3), ("lowbits", 14, 4), ("lowbits", 16, 4), ("random", 15, 1),
 ]
 
