@@ -93,7 +93,7 @@ KERNEL_SOURCES = {("k_coset", "c64"): ("kernels.cuh", "rotate.cu"),
                   ("k_coset", "c128"): ("coset_fx.cuh", "fixed64.cuh", "kernels.cuh", "rotate.cu"),
                   ("k_diag_sum", "c64"): ("kernels.cuh", "rotate.cu"),
                   ("k_diag_sum", "c128"): ("kernels.cuh", "rotate.cu"),
-                  ("k_expval", "c64"): ("reduce.cu",), ("k_expval", "c128"): ("reduce.cu",)}
+                  ("k_expval", "c64"): ("reduce.cu",), ("k_expval", "c128"): ("reduce.cu", "fixed64.cuh")}
 
 
 def kernel_source_digest(name: str, dtype: str):

@@ -114,6 +114,12 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
 
   std::vector<RotDev> rots;
   std::vector<DiagDev> diags;
+  rots.reserve(count);
+  p->order.reserve(count);
+  p->beta.reserve(count);
+  p->sigma.reserve(count);
+  p->ox.reserve(count);
+  p->oz.reserve(count);
   std::complex<double> scale(1.0, 0.0);
   double growth_since_fold = 0.0;
 
@@ -174,13 +180,14 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
       uint32_t u = 0;
       for (int b = 0; b < rb.d; ++b)
         if ((e.x >> rb.piv[b]) & 1ULL) u |= 1u << b;
+      // bit l of zt = parity(z & offset_l), offset_l = xor of the basis vectors
+      // selected by l: the xor of the index masks {l : bit b of l} over the
+      // basis vectors b with odd parity(z & basis_b)
+      static const uint32_t kSel[kDMax] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
       uint32_t zt = 0;
-      for (int l = 0; l < (1 << rb.d); ++l) {
-        uint64_t s = 0;
-        for (int b = 0; b < rb.d; ++b)
-          if ((l >> b) & 1) s ^= rb.basis[b];
-        zt |= (uint32_t)(popc64(s & e.z) & 1) << l;
-      }
+      for (int b = 0; b < rb.d; ++b)
+        if (popc64(rb.basis[b] & e.z) & 1) zt ^= kSel[b];
+      zt &= (rb.d >= 5) ? 0xFFFFFFFFu : ((1u << (1 << rb.d)) - 1u);
       int ny = popc64(e.x & e.z) & 3;
       int imag = (ny & 1) == 0;
       double ks = (ny == 0 || ny == 1) ? -1.0 : 1.0;  // kappa = (-i)^{nY+1}
@@ -300,8 +307,11 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
     e.x = it.x;
     e.z = it.z;
     e.t = std::tan(0.5 * a);
-    e.c = std::cos(0.5 * a);
-    double g = -std::log2(e.c);
+    // cos(a/2) = 1/sqrt(1 + tan^2) for |a/2| <= pi/4: the scale of exactly the
+    // rotation the tan form applies; growth bound -log2 cos = log2(1 + t^2) / 2
+    const double q = 1.0 + e.t * e.t;
+    e.c = 1.0 / std::sqrt(q);
+    double g = 0.5 * std::log2(q);
     p->order.push_back(it.idx);
     p->beta.push_back(a);
     p->sigma.push_back((int8_t)sp);
