@@ -168,8 +168,13 @@ int frame_get(sv_state *sv, uint64_t *xq, uint64_t *zq, int *phase);
  * rotations in a fullstate simulator" and App. "Amplitude update rule for
  * multi-qubit rotations").  Host arrays of length count.  Each rotation is rewritten by the frame
  * (sign flip where P anticommutes with Q), the list is compiled into fused
- * runs (same work as plan_create with fusion_depth = -1) and launched on the
- * handle's stream.  Returns before the device work finishes. */
+ * runs (the runs and launches of plan_create with fusion_depth = -1 followed by
+ * plan_apply, so the result is the same bit for bit) and launched on the
+ * handle's stream while the rest of the list is still being compiled: runs go
+ * out in batches, their records copied from pinned staging into a device
+ * buffer that the handle keeps for later calls (grown as needed, released by
+ * sv_free).  The host arrays may be reused when the call returns; it returns
+ * before the device work finishes. */
 int apply_pauli_rotations(sv_state *sv, const uint64_t *x, const uint64_t *z,
                           const double *angles, size_t count);
 

@@ -329,23 +329,32 @@ int launch_chain_t(sv_state *sv, const sv_plan *plan, const ChainDev &ch, uint64
 
 }  // namespace
 
+bool chains_enabled(const sv_plan *p) {
+  if (p->dtype != SV_C64 || p->n <= kChainDim) return false;
+  const char *env = std::getenv("PAULIROT_CHAIN");
+  return !(env && env[0] == '0');
+}
+
+bool chain_pair(const sv_plan *p, size_t i, ChainDev *out) {
+  const std::vector<RunDev> &runs = p->runs;
+  if (i + 1 >= runs.size() || !packable(runs[i]) || !packable(runs[i + 1]) ||
+      runs[i].count + runs[i + 1].count > kMaxRunRots)
+    return false;
+  return make_chain(p->n, runs[i], runs[i + 1], *out);
+}
+
 void build_chains(sv_plan *p) {
   p->steps.clear();
   p->chains.clear();
-  if (p->dtype != SV_C64 || p->n <= kChainDim) return;
-  const char *env = std::getenv("PAULIROT_CHAIN");
-  if (env && env[0] == '0') return;
-  const std::vector<RunDev> &runs = p->runs;
-  for (size_t i = 0; i < runs.size();) {
-    if (i + 1 < runs.size() && packable(runs[i]) && packable(runs[i + 1]) &&
-        runs[i].count + runs[i + 1].count <= kMaxRunRots) {
-      ChainDev ch;
-      if (make_chain(p->n, runs[i], runs[i + 1], ch)) {
-        p->steps.push_back({(int32_t)i, (int32_t)p->chains.size()});
-        p->chains.push_back(ch);
-        i += 2;
-        continue;
-      }
+  if (!chains_enabled(p)) return;
+  // greedy from the front: a run pairs with its successor when both fit
+  for (size_t i = 0; i < p->runs.size();) {
+    ChainDev ch;
+    if (chain_pair(p, i, &ch)) {
+      p->steps.push_back({(int32_t)i, (int32_t)p->chains.size()});
+      p->chains.push_back(ch);
+      i += 2;
+      continue;
     }
     p->steps.push_back({(int32_t)i, -1});
     ++i;

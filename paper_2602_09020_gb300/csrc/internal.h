@@ -221,6 +221,13 @@ struct sv_state {
   // packed complex64 passes launched on this handle (their parity sets the
   // direction the next one walks the cosets in)
   uint32_t packed_passes = 0;
+  // rotation records of apply_pauli_rotations: device buffer and pinned
+  // staging, kept for the next call; the event follows the last copy
+  void *d_rec = nullptr;
+  size_t d_rec_cap = 0;
+  void *h_rec = nullptr;
+  size_t h_rec_cap = 0;
+  cudaEvent_t rec_copied = nullptr;
   // tracing
   bool tracing = false;
   bool trace_blocks = false;  // one event per change of kernel instead of per launch
@@ -268,6 +275,9 @@ int launch_run(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t fx
 // chained passes (chain.cu): pair up consecutive runs of a complex64 plan
 // (fills plan->steps and plan->chains), and launch one chained pass
 void build_chains(sv_plan *plan);
+bool chains_enabled(const sv_plan *plan);
+// runs i and i + 1 of the plan as one chained pass, if they qualify
+bool chain_pair(const sv_plan *plan, size_t i, ChainDev *out);
 int launch_chain(sv_state *sv, const sv_plan *plan, const ChainDev &chain, uint64_t fx, uint64_t fz);
 int prepare_tables(int dtype);
 int table_pointer(int dtype, const void **out);
@@ -276,9 +286,19 @@ int launch_materialize(sv_state *sv, uint64_t x, uint64_t z, int q);
 int launch_set_basis(sv_state *sv, uint64_t k);
 
 // plan building (plan.cu)
-// upload = false: plan on the host only (no device allocation, no upload)
+// Receives the plan's runs while build_plan makes them: run(p, rots, diags) after
+// each run is appended (its rotation records are final; the newest run's fold
+// may still change), finish(p, rots, diags) once the plan is complete.
+struct PlanSink {
+  virtual int run(sv_plan *p, const std::vector<RotDev> &rots, const std::vector<DiagDev> &diags) = 0;
+  virtual int finish(sv_plan *p, const std::vector<RotDev> &rots, const std::vector<DiagDev> &diags) = 0;
+  virtual ~PlanSink() = default;
+};
+// upload = false: plan on the host only (no device allocation, no upload);
+// with a sink the records go to the sink instead of a device copy of the plan
 int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *z,
-               const double *theta, size_t count, int fusion_depth, cudaStream_t stream, bool upload = true);
+               const double *theta, size_t count, int fusion_depth, cudaStream_t stream, bool upload = true,
+               PlanSink *sink = nullptr);
 int apply_plan(sv_state *sv, sv_plan *plan);
 int validate_masks(int n, const uint64_t *x, const uint64_t *z, size_t count);
 // tuned fusion depth for (n, dtype), or -1 if none is recorded (tune.cu)

@@ -84,7 +84,8 @@ struct Eff {
 }  // namespace
 
 int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *z,
-               const double *theta, size_t count, int fusion_depth, cudaStream_t stream, bool upload) {
+               const double *theta, size_t count, int fusion_depth, cudaStream_t stream, bool upload,
+               PlanSink *sink) {
   (void)stream;
   if (n < 1 || n > max_qubits(dtype)) return fail(SV_EINVAL, "bad n_qubits %d", n);
   if (count && (!x || !z || !theta)) return fail(SV_EINVAL, "NULL rotation arrays");
@@ -163,8 +164,8 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
   Pauli qp;  // frame factors taken out so far (plan frame)
   const double gcap = fold_half(dtype);
 
-  auto finish_coset_run = [&](bool force_fold) {
-    if (rb.members.empty() && !force_fold) return;
+  auto finish_coset_run = [&](bool force_fold) -> int {
+    if (rb.members.empty() && !force_fold) return SV_OK;
     RunDev r;
     std::memset(&r, 0, sizeof(r));
     r.kind = 0;
@@ -216,12 +217,14 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
     }
     p->runs.push_back(r);
     rb.reset();
+    return sink ? sink->run(p, rots, diags) : SV_OK;
   };
 
   size_t k = 0;
   while (k < items.size()) {
     if (in_diag[k]) {
-      finish_coset_run(false);
+      rc = finish_coset_run(false);
+      if (rc) return rc;
       size_t b = k;
       while (b < items.size() && in_diag[b] && b - k < (size_t)kMaxDiagRots) ++b;
       // one phase-sum run over items[k, b); all diagonal, so any order is exact
@@ -277,6 +280,10 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
       }
       p->runs.push_back(r);
       p->n_diag_runs++;
+      if (sink) {
+        rc = sink->run(p, rots, diags);
+        if (rc) return rc;
+      }
       k = b;
       continue;
     }
@@ -326,7 +333,8 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
       if (r != 0 && rb.d >= dmax) fits = false;
     }
     if (!fits) {
-      finish_coset_run(false);
+      rc = finish_coset_run(false);
+      if (rc) return rc;
       r = it.x ? rb.reduce(it.x) : 0;
     }
     if (r != 0) rb.add_vector(r);
@@ -338,7 +346,8 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
   }
   bool need_fold = std::abs(scale - std::complex<double>(1.0, 0.0)) != 0.0;
   if (!rb.members.empty()) {
-    finish_coset_run(need_fold);
+    rc = finish_coset_run(need_fold);
+    if (rc) return rc;
   } else if (need_fold) {
     if (!p->runs.empty()) {
       RunDev &last = p->runs.back();
@@ -349,13 +358,15 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
       last.fold_re = f.real();
       last.fold_im = f.imag();
     } else {
-      finish_coset_run(true);  // an empty d = 0 run that only scales
+      rc = finish_coset_run(true);  // an empty d = 0 run that only scales
+      if (rc) return rc;
     }
   }
   p->frame = qp;
   p->n_effective = items.size();
   p->n_rots = rots.size();
   p->n_diag = diags.size();
+  if (sink) return sink->finish(p, rots, diags);
   build_chains(p);
   if (!upload) return SV_OK;
 
@@ -409,6 +420,103 @@ int apply_plan(sv_state *sv, sv_plan *plan) {
   sv->frame = f;
   return SV_OK;
 }
+
+namespace {
+
+// apply_pauli_rotations without a stored plan: the planner hands over each run
+// as it is made, and runs are launched in batches while it works on the rest
+// of the list.  The launches (kernels, parameters, order, pairing into chained
+// passes) are the ones plan_create + plan_apply make for the same list, so the
+// result is the same bit for bit; the planning time overlaps the device work
+// instead of preceding it.  Records reach the device by asynchronous copies from
+// the handle's pinned staging buffer, on the handle's stream, before the runs
+// that read them.
+struct StreamLauncher final : PlanSink {
+  static constexpr size_t kBatch = 16;  // runs per copy-and-launch batch
+  sv_state *sv;
+  Pauli q0;
+  size_t rot_slots;
+  bool init = false, chain = false;
+  size_t next = 0;    // runs [0, next) are launched or pending
+  long pending = -1;  // a run waiting to be paired with its successor
+  size_t up_rots = 0, up_diags = 0;
+
+  StreamLauncher(sv_state *s, size_t slots) : sv(s), q0(s->frame), rot_slots(slots) {}
+
+  int upload(const std::vector<RotDev> &rots, const std::vector<DiagDev> &diags) {
+    char *h = (char *)sv->h_rec, *d = (char *)sv->d_rec;
+    if (rots.size() > up_rots) {
+      const size_t off = up_rots * sizeof(RotDev), nb = (rots.size() - up_rots) * sizeof(RotDev);
+      std::memcpy(h + off, rots.data() + up_rots, nb);
+      PR_CUDA(cudaMemcpyAsync(d + off, h + off, nb, cudaMemcpyHostToDevice, sv->stream));
+      up_rots = rots.size();
+    }
+    if (diags.size() > up_diags) {
+      const size_t off = rot_slots * sizeof(RotDev) + up_diags * sizeof(DiagDev);
+      const size_t nb = (diags.size() - up_diags) * sizeof(DiagDev);
+      std::memcpy(h + off, diags.data() + up_diags, nb);
+      PR_CUDA(cudaMemcpyAsync(d + off, h + off, nb, cudaMemcpyHostToDevice, sv->stream));
+      up_diags = diags.size();
+    }
+    PR_CUDA(cudaEventRecord(sv->rec_copied, sv->stream));
+    return SV_OK;
+  }
+
+  // launch runs [next, upto), pairing them as build_chains does
+  int launch_upto(sv_plan *p, size_t upto) {
+    for (; next < upto; ++next) {
+      int rc;
+      if (pending >= 0) {
+        ChainDev ch;
+        const bool paired = chain_pair(p, (size_t)pending, &ch);
+        rc = paired ? launch_chain(sv, p, ch, q0.x, q0.z) : launch_run(sv, p, p->runs[pending], q0.x, q0.z);
+        pending = -1;
+        if (rc) return rc;
+        if (paired) continue;
+      }
+      if (chain) {
+        pending = (long)next;
+        continue;
+      }
+      rc = launch_run(sv, p, p->runs[next], q0.x, q0.z);
+      if (rc) return rc;
+    }
+    return SV_OK;
+  }
+
+  int run(sv_plan *p, const std::vector<RotDev> &rots, const std::vector<DiagDev> &diags) override {
+    if (!init) {
+      chain = chains_enabled(p);
+      init = true;
+    }
+    // the newest run may still take the closing fold: keep it back
+    const size_t ready = p->runs.size() - 1;
+    if (ready < next + kBatch) return SV_OK;
+    int rc = upload(rots, diags);
+    return rc ? rc : launch_upto(p, ready);
+  }
+
+  int finish(sv_plan *p, const std::vector<RotDev> &rots, const std::vector<DiagDev> &diags) override {
+    if (!init) {
+      chain = chains_enabled(p);
+      init = true;
+    }
+    int rc = upload(rots, diags);
+    if (!rc) rc = launch_upto(p, p->runs.size());
+    if (!rc && pending >= 0) {
+      rc = launch_run(sv, p, p->runs[pending], q0.x, q0.z);
+      pending = -1;
+    }
+    if (rc) return rc;
+    // Q <- Q0 Qp (-1)^{<Qp, Q0>}, as apply_plan does
+    Pauli f = pauli_mul(q0, p->frame);
+    if (anticommute(p->frame.x, p->frame.z, q0.x, q0.z)) f.q = (f.q + 2) & 3;
+    sv->frame = f;
+    return SV_OK;
+  }
+};
+
+}  // namespace
 
 }  // namespace pr
 
@@ -484,11 +592,41 @@ int plan_sweeps(const sv_plan *plan, size_t *n_sweeps) {
 int apply_pauli_rotations(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *angles,
                           size_t count) {
   if (!sv) return fail(SV_EINVAL, "sv is NULL");
-  sv_plan *p = nullptr;
-  int rc = plan_create(&p, sv->n, sv->dtype, x, z, angles, count, -1, sv->stream);
-  if (rc) return rc;
-  rc = apply_plan(sv, p);
-  plan_free(p);
+  // the previous call's records must have left the staging buffer
+  if (sv->rec_copied) PR_CUDA(cudaEventSynchronize(sv->rec_copied));
+  const size_t slots = count > 0 ? count : 1;
+  const size_t need = slots * (sizeof(RotDev) + sizeof(DiagDev));
+  if (sv->d_rec_cap < need) {
+    if (sv->d_rec) PR_CUDA(cudaFree(sv->d_rec));  // synchronises with earlier launches
+    sv->d_rec = nullptr;
+    sv->d_rec_cap = 0;
+    if (cudaMalloc(&sv->d_rec, need) != cudaSuccess) {
+      cudaGetLastError();
+      sv->d_rec = nullptr;
+      return fail(SV_ENOMEM, "rotation record buffer allocation failed");
+    }
+    sv->d_rec_cap = need;
+  }
+  if (sv->h_rec_cap < need) {
+    if (sv->h_rec) PR_CUDA(cudaFreeHost(sv->h_rec));
+    sv->h_rec = nullptr;
+    sv->h_rec_cap = 0;
+    if (cudaHostAlloc(&sv->h_rec, need, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      sv->h_rec = nullptr;
+      return fail(SV_ENOMEM, "rotation record staging allocation failed");
+    }
+    sv->h_rec_cap = need;
+  }
+  if (!sv->rec_copied) PR_CUDA(cudaEventCreateWithFlags(&sv->rec_copied, cudaEventDisableTiming));
+  sv_plan p;
+  p.owns_device = false;
+  p.d_rots = (RotDev *)sv->d_rec;
+  p.d_diag = (DiagDev *)((char *)sv->d_rec + slots * sizeof(RotDev));
+  StreamLauncher L(sv, slots);
+  int rc = build_plan(&p, sv->n, sv->dtype, x, z, angles, count, -1, sv->stream, false, &L);
+  p.d_rots = nullptr;
+  p.d_diag = nullptr;
   return rc;
 }
 

@@ -262,6 +262,9 @@ int sv_free(sv_state *sv) {
   if (sv->h_results) cudaFreeHost(sv->h_results);
   if (sv->d_stage) cudaFree(sv->d_stage);
   if (sv->h_stage) cudaFreeHost(sv->h_stage);
+  if (sv->d_rec) cudaFree(sv->d_rec);
+  if (sv->h_rec) cudaFreeHost(sv->h_rec);
+  if (sv->rec_copied) cudaEventDestroy(sv->rec_copied);
   trace_release(sv);
   delete sv;
   return SV_OK;
