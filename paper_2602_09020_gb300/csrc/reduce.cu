@@ -29,6 +29,7 @@ namespace {
 constexpr int kExpD = 4;
 constexpr int kExpMaxTerms = 1024;
 constexpr int kExpMaxGroups = 1 << kExpD;
+constexpr int kPsumD = 3;  // coset dimension of the H psi runs
 
 template <typename R>
 struct Cx;
@@ -294,42 +295,98 @@ __global__ void k_finish(const double *__restrict__ partials, int n_blocks, doub
   }
 }
 
+// q 2^-K as binary64 rounded to nearest even, on the integer pipes (|q| < 2^63;
+// 2^-K and the result normal numbers): the value of (double)q * 2^-K without
+// the conversion and the multiply, which both occupy GB300's narrow FP64 pipe
+__device__ __forceinline__ double i64_ldexp(long long q, int K) {
+  const uint64_t sgn = (uint64_t)q & 0x8000000000000000ULL;
+  const uint64_t v = q < 0 ? (uint64_t)(-q) : (uint64_t)q;
+  const int lz = __clzll((long long)v);
+  const uint64_t nv = v << (lz & 63);
+  uint64_t m = nv >> 11;
+  const uint64_t rest = nv & 0x7ffULL;
+  m += (rest > 0x400ULL || (rest == 0x400ULL && (m & 1ULL))) ? 1ULL : 0ULL;
+  int e = 63 - lz - K;
+  const uint64_t carry = m >> 53;
+  m >>= carry;
+  e += (int)carry;
+  const uint64_t bits = sgn | ((uint64_t)(e + 1023) << 52) | (m & 0xfffffffffffffULL);
+  return v == 0 ? 0.0 : __longlong_as_double((long long)bits);
+}
+
 // dst += sum_g sum_{j in g} c_j i^{nY_j} s_j(k^x) src_{k^x}   (per element k)
-// One group of an H psi run on a coset: o_l += (sum_j c_j i^{nY_j} s_j(k_m)) a_m
-// with m = l ^ U for every element l.  The coefficient sum is exact in 64-bit
-// fixed point (each c_j held as round(c_j 2^K), K from the run's sum of |c_j|)
-// on the integer pipes: one conversion and scale per element and group.
+// One group of an H psi run on a coset: o_l += C(m) a_m with m = l ^ U and
+// C(m) = sum_j c_j i^{nY_j} s_j(k_m).  With k_m = rep ^ off_m the sign splits as
+// s_j(rep) (-1)^{sigma_j . m}, sigma_j,b = parity(z_j & basis_b), so C is the
+// Walsh-Hadamard transform over m of W[sigma] = sum over the group's terms with
+// that sigma of c_j i^{nY_j} s_j(rep): one signed add per term and coset, then
+// one transform per coset (real and imaginary parts apart), exact in 64-bit
+// fixed point (each c_j held as round(c_j 2^K), K from the run's sum of
+// |c_j|, so no partial sum or transform entry exceeds 2^62), and one
+// conversion per element and group.  Amplitudes are widened and coefficients
+// converted by integer work (widen_f64, i64_ldexp); the FP64 pipe does only the
+// complex multiply-adds.
+struct PsTermSm {
+  uint64_t z;
+  long long q;    // round(c_j 2^K), negated for nY = 2, 3 (mod 4)
+  uint32_t code;  // sigma_j | (nY odd) << D
+  uint32_t pad;
+};
+
+template <int N>
+__device__ __forceinline__ void psum_wht(long long *W) {
+#pragma unroll
+  for (int h = 1; h < N; h <<= 1) {
+#pragma unroll
+    for (int p = 0; p < N; ++p)
+      if (!(p & h)) {
+        const long long a = W[p], b = W[p | h];
+        W[p] = a + b;
+        W[p | h] = a - b;
+      }
+  }
+}
+
+#define PR_PSUM_W(K) \
+  case K:            \
+    if constexpr ((K) < 2 * E) W[K] += q; \
+    break;
+
 template <int U, int E, typename Idx>
 __device__ __forceinline__ void psum_group(const double2 (&a)[E], double2 (&o)[E], const ExpGroupDev &G,
-                                           const ExpTermSm *terms, Idx rep, double qscale) {
+                                           const PsTermSm *terms, Idx rep, int qk) {
+  long long W[2 * E];
+#pragma unroll
+  for (int k = 0; k < 2 * E; ++k) W[k] = 0;
+  for (int j = G.first; j < G.first + G.count; ++j) {
+    const PsTermSm t = terms[j];
+    const long long q = parity((uint64_t)rep & t.z) ? -t.q : t.q;
+    switch (t.code) {
+      PR_PSUM_W(0) PR_PSUM_W(1) PR_PSUM_W(2) PR_PSUM_W(3) PR_PSUM_W(4) PR_PSUM_W(5) PR_PSUM_W(6) PR_PSUM_W(7)
+      PR_PSUM_W(8) PR_PSUM_W(9) PR_PSUM_W(10) PR_PSUM_W(11) PR_PSUM_W(12) PR_PSUM_W(13) PR_PSUM_W(14)
+      PR_PSUM_W(15)
+      default: break;
+    }
+  }
+  // groups whose strings all have even (odd) nY have a real (imaginary)
+  // coefficient: one transform and half the FP64 multiply-adds
+  if (G.pad != 2) psum_wht<E>(W);
+  if (G.pad != 1) psum_wht<E>(W + E);
 #pragma unroll
   for (int l = 0; l < E; ++l) {
     constexpr int UU = U;
     const int m = l ^ UU;
-    long long qr = 0, qi = 0;
-    for (int j = G.first; j < G.first + G.count; ++j) {
-      const ExpTermSm t = terms[j];
-      const uint32_t s = (uint32_t)parity((uint64_t)rep & t.z) ^ ((t.zt >> m) & 1u);
-      const long long q = __double_as_longlong(t.coef);
-      const long long sq = (s & 1u) ? -q : q;
-      switch (t.imag & 3u) {
-        case 0: qr += sq; break;
-        case 1: qi += sq; break;
-        case 2: qr -= sq; break;
-        default: qi -= sq; break;
-      }
-    }
-    const double cr = (double)qr * qscale, ci = (double)qi * qscale;
     const double2 am = a[m];
-    // groups whose strings all have even (odd) nY have a real (imaginary)
-    // coefficient: half the FP64 multiply-adds
     if (G.pad == 1) {
+      const double cr = i64_ldexp(W[m], qk);
       o[l].x = fma(cr, am.x, o[l].x);
       o[l].y = fma(cr, am.y, o[l].y);
     } else if (G.pad == 2) {
+      const double ci = i64_ldexp(W[E + m], qk);
       o[l].x = fma(-ci, am.y, o[l].x);
       o[l].y = fma(ci, am.x, o[l].y);
     } else {
+      const double cr = i64_ldexp(W[m], qk), ci = i64_ldexp(W[E + m], qk);
       o[l].x = fma(cr, am.x, fma(-ci, am.y, o[l].x));
       o[l].y = fma(cr, am.y, fma(ci, am.x, o[l].y));
     }
@@ -338,7 +395,7 @@ __device__ __forceinline__ void psum_group(const double2 (&a)[E], double2 (&o)[E
 
 #define PR_PSUM_CASE(K)                                                  \
   case K:                                                                \
-    if constexpr ((K) < E) psum_group<(K), E, Idx>(a, o, G, terms, rep, run.qscale); \
+    if constexpr ((K) < E) psum_group<(K), E, Idx>(a, o, G, terms, rep, qk); \
     break;
 
 template <typename R, typename Idx, int D>
@@ -346,16 +403,20 @@ __global__ void __launch_bounds__(kThreads)
     k_pauli_sum(typename Cx<R>::T *__restrict__ dst, const typename Cx<R>::T *__restrict__ src, Idx n_cosets,
                 const ExpRunDev run, const ExpGroupDev *__restrict__ groups,
                 const ExpTermDev *__restrict__ gterms) {
+  static_assert(D <= kPsumD, "H psi cosets have at most 2^kPsumD elements");
   using C = typename Cx<R>::T;
   constexpr int E = 1 << D;
-  __shared__ ExpTermSm terms[kExpMaxTerms];
+  __shared__ PsTermSm terms[kExpMaxTerms];
   __shared__ ExpGroupDev sg[kExpMaxGroups];
   __shared__ Idx soff[E];
   int n_terms = 0;
   for (int g = 0; g < run.n_groups; ++g) n_terms = max(n_terms, groups[g].first + groups[g].count);
   for (int j = threadIdx.x; j < n_terms; j += blockDim.x) {
     const ExpTermDev t = gterms[j];
-    terms[j] = ExpTermSm{t.z, t.coef, t.zt, t.imag};
+    uint32_t sigma = 0;
+    for (int b = 0; b < D; ++b) sigma |= ((t.zt >> (1u << b)) & 1u) << b;
+    const long long q = __double_as_longlong(t.coef);
+    terms[j] = PsTermSm{t.z, (t.imag & 2u) ? -q : q, sigma | ((t.imag & 1u) << D), 0u};
   }
   if (threadIdx.x < run.n_groups) sg[threadIdx.x] = groups[threadIdx.x];
   if (threadIdx.x < E) {
@@ -365,6 +426,7 @@ __global__ void __launch_bounds__(kThreads)
     soff[threadIdx.x] = (Idx)s;
   }
   __syncthreads();
+  const int qk = 1023 - (int)((__double_as_longlong(run.qscale) >> 52) & 0x7ff);  // qscale = 2^-qk
   const Idx stride = (Idx)gridDim.x * blockDim.x;
   for (Idx c = (Idx)blockIdx.x * blockDim.x + threadIdx.x; c < n_cosets; c += stride) {
     Idx rep = c;
@@ -377,11 +439,11 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int l = 0; l < E; ++l) {
       const C v = src[rep ^ soff[l]];
-      a[l].x = (double)v.x;
-      a[l].y = (double)v.y;
+      a[l].x = widen_f64(v.x);
+      a[l].y = widen_f64(v.y);
       const C w = dst[rep ^ soff[l]];
-      o[l].x = (double)w.x;
-      o[l].y = (double)w.y;
+      o[l].x = widen_f64(w.x);
+      o[l].y = widen_f64(w.y);
     }
     for (int g = 0; g < run.n_groups; ++g) {
       const ExpGroupDev G = sg[g];
@@ -390,8 +452,6 @@ __global__ void __launch_bounds__(kThreads)
       switch (G.u) {
         PR_PSUM_CASE(0) PR_PSUM_CASE(1) PR_PSUM_CASE(2) PR_PSUM_CASE(3)
         PR_PSUM_CASE(4) PR_PSUM_CASE(5) PR_PSUM_CASE(6) PR_PSUM_CASE(7)
-        PR_PSUM_CASE(8) PR_PSUM_CASE(9) PR_PSUM_CASE(10) PR_PSUM_CASE(11)
-        PR_PSUM_CASE(12) PR_PSUM_CASE(13) PR_PSUM_CASE(14) PR_PSUM_CASE(15)
         default: break;
       }
     }
@@ -440,7 +500,7 @@ void plan_groups(const sv_state *sv, const uint64_t *x, const uint64_t *z, const
   }
   std::vector<char> used(groups.size(), 0);
   size_t left = groups.size();
-  const int dmax = std::min(kExpD, sv->n);
+  const int dmax = std::min(mode == 1 ? kPsumD : kExpD, sv->n);
   while (left > 0 || runs.empty()) {
     HostExpRun r;
     std::memset(&r.dev, 0, sizeof(r.dev));
@@ -691,7 +751,7 @@ int prepare(sv_state *sv, const uint64_t *x, const uint64_t *z, const double *c,
       }
     }
   }
-  D = std::min(kExpD, sv->n);
+  D = std::min(mode == 1 ? kPsumD : kExpD, sv->n);
   pad_runs(sv->n, D, runs);
   recode_runs(runs, gx);
   return SV_OK;
@@ -1470,8 +1530,7 @@ static int pauli_sum_d(sv_state *dst, sv_state *src, int D, const std::vector<Ho
   switch (D) {
     case 1: return run_pauli_sum_t<R, Idx, 1>(dst, src, runs, dg, dt);
     case 2: return run_pauli_sum_t<R, Idx, 2>(dst, src, runs, dg, dt);
-    case 3: return run_pauli_sum_t<R, Idx, 3>(dst, src, runs, dg, dt);
-    default: return run_pauli_sum_t<R, Idx, kExpD>(dst, src, runs, dg, dt);
+    default: return run_pauli_sum_t<R, Idx, kPsumD>(dst, src, runs, dg, dt);
   }
 }
 
