@@ -28,7 +28,7 @@ def test_block_trace_counts_match_launch_trace(dtype):
     sv = capi.sv_alloc(n, dtype, stream)
     plan = capi.plan_create(n, dtype, rx, rz, rt, -1, stream)
     try:
-        _, n_runs, _ = capi.plan_stats(plan)
+        n_runs = capi.plan_sweeps(plan)  # passes over the state: a chained pass applies several runs
         per_launch = traced_apply(sv, plan, ham, False)
         per_block = traced_apply(sv, plan, ham, True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -50,8 +50,7 @@ def test_block_trace_counts_match_launch_trace(dtype):
         assert per_launch[k][0] == per_block[k][0], k           # launches
         assert per_launch[k][2] == pytest.approx(per_block[k][2])  # bytes
         assert per_block[k][1] > 0
-    rot_launches = sum(v[0] for k, v in per_block.items() if k.startswith(("k_coset", "k_diag_sum")))
-    rot_launches += 2 * per_block.get("k_chain2", (0,))[0]  # a chained pass applies two runs
+    rot_launches = sum(v[0] for k, v in per_block.items() if k.startswith(("k_coset", "k_diag_sum", "k_chain")))
     assert rot_launches == n_runs
     # the blocks of one plan application tile the region between the two events
     total = sum(v[1] for v in rows.values())
