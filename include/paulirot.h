@@ -329,8 +329,7 @@ int expval_pauli_sum(sv_state *sv, const uint64_t *x, const uint64_t *z, const d
  * terms whose x-masks span <= 4 dimensions); larger requests fail with
  * SV_EINVAL and a message, before any device work.
  * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.
+ * (cudaGetSymbolAddress) with that device current.
  * Sharing: every call uses the same array and it keeps the last call's
  * contents; nothing in it needs to start at zero (every value is written before
  * it is read).  Calls that overlap on the GPU (other host threads, other streams)

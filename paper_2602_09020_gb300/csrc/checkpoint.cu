@@ -26,6 +26,8 @@
 #include <cstring>
 #include <string>
 
+#include <unistd.h>
+
 #include "internal.h"
 
 namespace pr {
@@ -155,8 +157,9 @@ int sv_save(sv_state *sv, const char *path, uint64_t tag) {
   put_u64(hdr + 48, (uint64_t)total);
   put_u64(hdr + 56, h);
   put_u64(hdr + 64, fnv_words(kFnvBasis, hdr, 64));
+  // on disk before the rename makes it the checkpoint
   const bool ok = std::fseek(out.f, 0, SEEK_SET) == 0 && std::fwrite(hdr, 1, kHeader, out.f) == kHeader &&
-                  std::fflush(out.f) == 0;
+                  std::fflush(out.f) == 0 && fsync(fileno(out.f)) == 0;
   std::fclose(out.f);
   out.f = nullptr;
   if (!ok || std::rename(tmp.c_str(), path) != 0) {
