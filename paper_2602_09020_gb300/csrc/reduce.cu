@@ -927,6 +927,9 @@ __global__ void __launch_bounds__(kWThreads, 4)
     k_expval_fix(const float2 *__restrict__ amp, Idx n_tiles, const WhtRunDev run,
                  const WhtGroupDev *__restrict__ ggroups, const WhtTermDev *__restrict__ gterms, int K,
                  long long *__restrict__ partials, int reverse) {
+  // consecutive runs only read the state and write their own partials: the
+  // next run may start while this one drains (expval_fix_t launches them)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __shared__ WhtGroupDev groups[kWGroups];
   __shared__ Idx tz[kWTerms];
   __shared__ int tslot[kWTerms];
@@ -989,6 +992,9 @@ __global__ void __launch_bounds__(kWThreads, 4)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) partials[(size_t)blockIdx.x * kWTerms + j] = v;
   }
+  // the grid completes only after the previous run has: completion of the last
+  // run then implies completion of them all
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ---- complex128 <H> on the same plan, in 64-bit fixed point -------------------
@@ -1073,6 +1079,7 @@ __global__ void __launch_bounds__(kWThreads, 4)
     k_expval_fx128(const double2 *__restrict__ amp, Idx n_tiles, const WhtRunDev run,
                    const WhtGroupDev *__restrict__ ggroups, const WhtTermDev *__restrict__ gterms, int S,
                    long long *__restrict__ partials, int reverse) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __shared__ WhtGroupDev groups[kWGroups];
   __shared__ Idx tz[kWTerms];
   __shared__ int tslot[kWTerms];
@@ -1141,6 +1148,7 @@ __global__ void __launch_bounds__(kWThreads, 4)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) partials[(size_t)blockIdx.x * kWTerms + j] = v;
   }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // <a|a> of a complex128 state in FP64, per block (only used to pick S)
@@ -1442,15 +1450,27 @@ int expval_fix_t(sv_state *sv, const std::vector<FixRunHost> &runs, double *ener
   for (size_t r = 0; r < runs.size(); ++r) {
     const char *base = (const char *)sv->d_stage + off[r];
     const int tr = trace_begin(sv, KN_EXPVAL);
+    // programmatic dependent launches: a run's CTAs start as the previous
+    // run's last CTAs drain (the grid never exceeds what the GPU holds at
+    // once, so no waiting CTA can keep a pending one from running)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kWThreads);
+    cfg.stream = sv->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int rev = (int)((r + 1) & 1);
+    long long *pr = part + (size_t)kWTerms * blocks * r;
     if (c128)
-      k_expval_fx128<Idx><<<blocks, kWThreads, 0, sv->stream>>>(
-          (const double2 *)sv->amps, (Idx)n_tiles, runs[r].dev, (const WhtGroupDev *)base,
-          (const WhtTermDev *)(base + kGroupBytes), S, part + (size_t)kWTerms * blocks * r, (int)((r + 1) & 1));
+      PR_CUDA(cudaLaunchKernelEx(&cfg, k_expval_fx128<Idx>, (const double2 *)sv->amps, (Idx)n_tiles, runs[r].dev,
+                                 (const WhtGroupDev *)base, (const WhtTermDev *)(base + kGroupBytes), S, pr, rev));
     else
-      k_expval_fix<Idx><<<blocks, kWThreads, 0, sv->stream>>>(
-          (const float2 *)sv->amps, (Idx)n_tiles, runs[r].dev, (const WhtGroupDev *)base,
-          (const WhtTermDev *)(base + kGroupBytes), 14 - S, part + (size_t)kWTerms * blocks * r, (int)((r + 1) & 1));
-    PR_CHECK_LAUNCH();
+      PR_CUDA(cudaLaunchKernelEx(&cfg, k_expval_fix<Idx>, (const float2 *)sv->amps, (Idx)n_tiles, runs[r].dev,
+                                 (const WhtGroupDev *)base, (const WhtTermDev *)(base + kGroupBytes), 14 - S, pr,
+                                 rev));
     trace_end(sv, tr, KN_EXPVAL, (c128 ? 16.0 : 8.0) * (double)n_amps);
   }
   {

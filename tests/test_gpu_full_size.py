@@ -89,6 +89,44 @@ def test_n24_trotter_c128_and_c64_against_oracle():
     assert abs(e64 - e_orc) <= 1e-4 and abs(n64 - 1.0) <= 1e-4
 
 
+def test_n24_c64_launch_paths_agree_bitwise():
+    """The headline workload through its three launch paths: plan_create +
+    plan_apply (two-run passes), the one-shot apply_pauli_rotations (runs
+    launched while the list is planned) and plan_apply with chaining off
+    (PAULIROT_CHAIN=0, one pass per run).  All three states must be equal bit
+    for bit; the test above ties the first one to the oracle."""
+    ham = synth.jw_hamiltonian(24, 2000, 1)
+    rx, rz, rt = capi.trotter_expand(ham.x, ham.z, ham.c, 0.05, 10, 1, False)
+    stream = torch.cuda.current_stream().cuda_stream
+    outs = []
+    for mode in ("plan", "oneshot", "unchained"):
+        t, h = _torch_state(24, "c64", stream)
+        capi.sv_set_basis_state(h, synth.hartree_fock_index(12))
+        if mode == "oneshot":
+            assert capi.plan_tuned_depth(24, "c64")[0] == 4  # what plan_create(-1) takes
+            capi.apply_pauli_rotations(h, rx, rz, rt)
+        else:
+            old = os.environ.get("PAULIROT_CHAIN")
+            os.environ["PAULIROT_CHAIN"] = "0" if mode == "unchained" else "1"
+            try:
+                p = capi.plan_create(24, "c64", rx, rz, rt, 4, stream)
+            finally:
+                if old is None:
+                    os.environ.pop("PAULIROT_CHAIN", None)
+                else:
+                    os.environ["PAULIROT_CHAIN"] = old
+            sweeps, runs = capi.plan_sweeps(p), capi.plan_stats(p)[1]
+            assert (sweeps < runs) if mode == "plan" else (sweeps == runs)
+            capi.plan_apply(h, p)
+            capi.plan_free(p)
+        capi.sv_materialize(h)
+        torch.cuda.synchronize()
+        capi.sv_free(h)
+        outs.append(t)
+    for t in outs[1:]:
+        assert torch.equal(outs[0].view(torch.int64), t.view(torch.int64))
+
+
 def test_n29_second_order_c64_vs_c128_and_n30_norm():
     stream = torch.cuda.current_stream().cuda_stream
     hams = {29: synth.jw_hamiltonian(29, 5000, 1), 30: synth.jw_hamiltonian(30, 5000, 1)}
