@@ -181,6 +181,20 @@ __device__ __forceinline__ double tree_sum(double (&v)[N]) {
   return v[0];
 }
 
+// Compensated FP32 sum (Neumaier): s + c equals the sum of the added values up
+// to O(n u^2) of their magnitudes (u = 2^-24), so a coset's complex64 gradient
+// terms reach the FP64 accumulator as two exactly widened floats and one FP64
+// add instead of one FP64 add per term (GB300's FP64 pipe is narrow)
+struct CompSum32 {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return widen_f64(s) + widen_f64(c); }
+};
+
 // Im(conj(a) b)
 template <typename V>
 __device__ __forceinline__ typename AdjScalar<V>::T im_conj_mul(V a, V b) {
@@ -212,14 +226,17 @@ __device__ __forceinline__ typename AdjScalar<V>::T im_conj_ipow(V a, V b) {
 // so the phase costs swaps and negations only.  The factor cos(beta/2) is left
 // out: inside a run both vectors carry the same known scale, which the host
 // folds into each gradient and the kernel into the stored states.  Each
-// element's gradient term is formed in the state's precision and added to the
-// FP64 accumulator g.
+// element's gradient term is formed in the state's precision; complex128 terms
+// are summed in FP64, complex64 terms in a compensated FP32 sum per coset that
+// reaches FP64 once per coset and rotation.
 template <int U, int K, typename V>
 __device__ __forceinline__ void adj_rot(V (&p)[1 << kAdjD], V (&l)[1 << kAdjD], const AdjRotDev &r, int sig,
                                         double &g) {
   using S = typename AdjScalar<V>::T;
   constexpr int E = 1 << kAdjD;
   const S t = (S)r.t;
+  constexpr bool F32 = sizeof(S) == 4;
+  CompSum32 acc;
   if constexpr (U == 0) {
     double part[E];
 #pragma unroll
@@ -228,11 +245,17 @@ __device__ __forceinline__ void adj_rot(V (&p)[1 << kAdjD], V (&l)[1 << kAdjD], 
       const S ts = neg ? -t : t;
       const V pe = p[e], le = l[e];
       const S ge = im_conj_mul(le, pe);
-      part[e] = widen_f64(neg ? -ge : ge);
+      if constexpr (F32)
+        acc.add(neg ? -ge : ge);
+      else
+        part[e] = widen_f64(neg ? -ge : ge);
       p[e] = adj_vec<V>(pe.x - ts * pe.y, pe.y + ts * pe.x);
       l[e] = adj_vec<V>(le.x - ts * le.y, le.y + ts * le.x);
     }
-    g = tree_sum(part);  // g enters as 0: no add of zero
+    if constexpr (F32)
+      g = acc.value();
+    else
+      g = tree_sum(part);  // g enters as 0: no add of zero
   } else {
     constexpr int H = adj_high_bit(U);
     double part[E / 2];
@@ -243,7 +266,12 @@ __device__ __forceinline__ void adj_rot(V (&p)[1 << kAdjD], V (&l)[1 << kAdjD], 
       const bool ne = (sig ^ (int)(r.zt >> e)) & 1, nm = (sig ^ (int)(r.zt >> m)) & 1;
       const V pe = p[e], pm = p[m], le = l[e], lm = l[m];
       const S ge = im_conj_ipow<K>(le, pm), gm = im_conj_ipow<K>(lm, pe);
-      part[q] = widen_f64(nm ? -ge : ge) + widen_f64(ne ? -gm : gm);
+      if constexpr (F32) {
+        acc.add(nm ? -ge : ge);
+        acc.add(ne ? -gm : gm);
+      } else {
+        part[q] = widen_f64(nm ? -ge : ge) + widen_f64(ne ? -gm : gm);
+      }
       const S te = ne ? -t : t, tm = nm ? -t : t;
       const V wpm = ipow<K + 1>(pm), wpe = ipow<K + 1>(pe), wlm = ipow<K + 1>(lm), wle = ipow<K + 1>(le);
       p[e] = adj_vec<V>(pe.x + tm * wpm.x, pe.y + tm * wpm.y);
@@ -251,7 +279,10 @@ __device__ __forceinline__ void adj_rot(V (&p)[1 << kAdjD], V (&l)[1 << kAdjD], 
       l[e] = adj_vec<V>(le.x + tm * wlm.x, le.y + tm * wlm.y);
       l[m] = adj_vec<V>(lm.x + te * wle.x, lm.y + te * wle.y);
     }
-    g = tree_sum(part);  // g enters as 0: no add of zero
+    if constexpr (F32)
+      g = acc.value();
+    else
+      g = tree_sum(part);  // g enters as 0: no add of zero
   }
 }
 
