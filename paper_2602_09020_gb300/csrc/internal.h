@@ -222,12 +222,14 @@ struct sv_state {
   // direction the next one walks the cosets in)
   uint32_t packed_passes = 0;
   // rotation records of apply_pauli_rotations: device buffer and pinned
-  // staging, kept for the next call; the event follows the last copy
+  // staging, kept for the next call; events after the last copy and after the
+  // last launch that reads the buffer
   void *d_rec = nullptr;
   size_t d_rec_cap = 0;
   void *h_rec = nullptr;
   size_t h_rec_cap = 0;
   cudaEvent_t rec_copied = nullptr;
+  cudaEvent_t rec_done = nullptr;
   // tracing
   bool tracing = false;
   bool trace_blocks = false;  // one event per change of kernel instead of per launch

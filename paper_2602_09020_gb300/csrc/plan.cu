@@ -619,6 +619,13 @@ int apply_pauli_rotations(sv_state *sv, const uint64_t *x, const uint64_t *z, co
     sv->h_rec_cap = need;
   }
   if (!sv->rec_copied) PR_CUDA(cudaEventCreateWithFlags(&sv->rec_copied, cudaEventDisableTiming));
+  if (!sv->rec_done) {
+    PR_CUDA(cudaEventCreateWithFlags(&sv->rec_done, cudaEventDisableTiming));
+  } else {
+    // the previous call's passes read the device buffer, maybe on another
+    // stream: this call's copies into it wait for them
+    PR_CUDA(cudaStreamWaitEvent(sv->stream, sv->rec_done, 0));
+  }
   sv_plan p;
   p.owns_device = false;
   p.d_rots = (RotDev *)sv->d_rec;
@@ -627,6 +634,9 @@ int apply_pauli_rotations(sv_state *sv, const uint64_t *x, const uint64_t *z, co
   int rc = build_plan(&p, sv->n, sv->dtype, x, z, angles, count, -1, sv->stream, false, &L);
   p.d_rots = nullptr;
   p.d_diag = nullptr;
+  // after the last launch of this call, also when it stopped early
+  const cudaError_t er = cudaEventRecord(sv->rec_done, sv->stream);
+  if (!rc && er != cudaSuccess) return fail(SV_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(er));
   return rc;
 }
 

@@ -265,6 +265,7 @@ int sv_free(sv_state *sv) {
   if (sv->d_rec) cudaFree(sv->d_rec);
   if (sv->h_rec) cudaFreeHost(sv->h_rec);
   if (sv->rec_copied) cudaEventDestroy(sv->rec_copied);
+  if (sv->rec_done) cudaEventDestroy(sv->rec_done);
   trace_release(sv);
   delete sv;
   return SV_OK;

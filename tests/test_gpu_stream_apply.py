@@ -65,3 +65,35 @@ def test_streamed_apply_equals_plan_apply(orc, n, dtype):
     finally:
         capi.sv_free(a)
         capi.sv_free(b)
+
+
+def test_streamed_apply_after_a_stream_switch():
+    """The handle's record buffer is reused by the next call, which may run on
+    another stream (sv_set_stream): its copies wait for the previous call's
+    passes, so a long list on one stream followed at once by a short one on
+    another gives the sequential result bit for bit."""
+    import torch
+    n = 18
+    ham = synth.jw_hamiltonian(n, 600, seed=5)
+    xa, za, ta = capi.trotter_expand(ham.x, ham.z, ham.c, 0.05, 4, 1, False)
+    xb, zb = random_paulis(n, 200, seed=6, span_dim=4)
+    tb = np.random.default_rng(6).uniform(-2, 2, size=200)
+    psi0 = synth.random_state(n, 7).astype(np.complex64)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    sv = capi.sv_alloc(n, "c64", s1.cuda_stream)
+    ref = capi.sv_alloc(n, "c64")
+    try:
+        capi.sv_from_host(sv, psi0)
+        capi.sv_from_host(ref, psi0)
+        capi.apply_pauli_rotations(sv, xa, za, ta)
+        capi.sv_set_stream(sv, s2.cuda_stream)
+        capi.apply_pauli_rotations(sv, xb, zb, tb)
+        for x, z, t in ((xa, za, ta), (xb, zb, tb)):
+            p = capi.plan_create(n, "c64", x, z, t, -1)
+            capi.plan_apply(ref, p)
+            capi.plan_free(p)
+        got, want = capi.sv_to_host(sv, False), capi.sv_to_host(ref, False)
+        assert np.array_equal(got.view(np.uint8), want.view(np.uint8))
+    finally:
+        capi.sv_free(sv)
+        capi.sv_free(ref)
