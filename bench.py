@@ -354,7 +354,11 @@ def run_ours(a):
                     "frac": tflops / peak, "peak_source": src,
                     "hbm": {"achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                             "frac": achieved / pk["hbm_gbs"], "peak_source": pk["source"]},
-                    "runs_per_sweep": 2}
+                    "runs_per_sweep": 2,
+                    # the bytes the two runs would move as one-run passes, over
+                    # the chained pass's time: the HBM rate one-run passes would
+                    # need to match it
+                    "run_equivalent_hbm_frac": 2.0 * achieved / pk["hbm_gbs"]}
         if dtype == "c128" and name.startswith("k_coset"):
             # the complex128 pass runs its products on the integer pipes: per
             # amplitude and rotation two 62-bit fixed-point products of three
