@@ -417,9 +417,9 @@ int batch_inspect(const int *n_qubits, const size_t *rotations, const size_t *pa
 
 /* Shape of the last batched launch: CTAs in the grid, states that spanned
  * several CTAs, and how it was launched: 1 = cooperative launch replayed from a
- * CUDA graph, 2 = plain launch of the same grid replayed from a graph, 0 = no
- * graph, negative = graph capture failed with that cudaError_t (launched
- * directly instead). */
+ * CUDA graph, 0 = no graph, negative = graph capture failed with that
+ * cudaError_t (the cooperative launch then runs directly; a plain launch, whose
+ * CTAs need not all be resident at once, is never used for the barriers). */
 int batch_info(int *grid_ctas, int *multi_cta_states, int *graph_used);
 
 /* ---- tracing (not in the paper) --------------------------------------------------------- */

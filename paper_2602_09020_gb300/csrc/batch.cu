@@ -191,7 +191,6 @@ struct BatchCache {
   int skip_state = -1;
   int multi_cta_states = 0;
   bool graph_ok = true;
-  bool coop = true;          // cooperative attribute on the launch
   int capture_error = 0;     // cudaError_t of the first failed capture step (0 = none)
 
   void release() {
@@ -243,7 +242,7 @@ int batch_launch(BatchCache &b, cudaStream_t s) {
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = b.coop ? 1 : 0;
+  cfg.numAttrs = 1;
   PR_CUDA(cudaLaunchKernelExC(&cfg, (const void *)k_batch<R, Idx>, args));
   return SV_OK;
 }
@@ -481,11 +480,11 @@ int batch_run_ex(sv_state **states, sv_plan **plans, size_t count, int use_graph
   }
   cudaStream_t s = states[0]->stream;
   if (use_graph && s != nullptr && b.graph_ok) {
-    // capture once; a cooperative launch first, then (if the driver cannot
-    // capture it) a plain launch of the same grid: the grid never exceeds what
-    // the device holds at once and every wait is bounded either way
-    for (int attempt = 0; attempt < 2 && !b.graph && b.graph_ok; ++attempt) {
-      b.coop = attempt == 0;
+    // capture the cooperative launch once.  A plain launch of the same grid is
+    // never captured instead: its per-state barriers would rely on every CTA
+    // being resident together, which only the cooperative launch guarantees;
+    // when the capture fails the cooperative launch runs without a graph.
+    if (!b.graph) {
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
@@ -495,24 +494,21 @@ int batch_run_ex(sv_state **states, sv_plan **plans, size_t count, int use_graph
           cudaError_t le = cudaGetLastError();
           if (!b.capture_error) b.capture_error = (int)(e2 != cudaSuccess ? e2 : (le != cudaSuccess ? le : cudaErrorUnknown));
           if (g) cudaGraphDestroy(g);
-          continue;
-        }
-        e = cudaGraphInstantiate(&b.graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-          if (!b.capture_error) b.capture_error = (int)e;
-          cudaGetLastError();
-          b.graph = nullptr;
+          g = nullptr;
+        } else {
+          e = cudaGraphInstantiate(&b.graph, g, 0);
+          cudaGraphDestroy(g);
+          if (e != cudaSuccess) {
+            if (!b.capture_error) b.capture_error = (int)e;
+            cudaGetLastError();
+            b.graph = nullptr;
+          }
         }
       } else {
         if (!b.capture_error) b.capture_error = (int)e;
         cudaGetLastError();
-        b.graph_ok = false;
       }
-    }
-    if (!b.graph) {
-      b.graph_ok = false;
-      b.coop = true;
+      if (!b.graph) b.graph_ok = false;
     }
     if (b.graph) {
       PR_CUDA(cudaGraphLaunch(b.graph, s));
@@ -521,7 +517,6 @@ int batch_run_ex(sv_state **states, sv_plan **plans, size_t count, int use_graph
       if (rc) return rc;
     }
   } else {
-    b.coop = true;
     rc = enqueue(b, s);
     if (rc) return rc;
   }
@@ -577,10 +572,9 @@ int batch_info(int *grid_ctas, int *multi_cta_states, int *graph_used) {
   std::lock_guard<std::mutex> lk(g_batch_mu);
   if (grid_ctas) *grid_ctas = g_batch.grid;
   if (multi_cta_states) *multi_cta_states = g_batch.multi_cta_states;
-  // 1 = cooperative launch in a graph, 2 = plain launch in a graph, 0 = no graph;
-  // -e = capture failed with cudaError_t e
-  if (graph_used)
-    *graph_used = g_batch.graph ? (g_batch.coop ? 1 : 2) : (g_batch.capture_error ? -g_batch.capture_error : 0);
+  // 1 = cooperative launch in a graph, 0 = no graph; -e = capture failed with
+  // cudaError_t e (the cooperative launch then runs without a graph)
+  if (graph_used) *graph_used = g_batch.graph ? 1 : (g_batch.capture_error ? -g_batch.capture_error : 0);
   return SV_OK;
 }
 
