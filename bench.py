@@ -17,8 +17,10 @@ Arms:
   --impl reference   the FP64 CPU oracle (gate-decomposed), on a bounded
                      sample of the same rotation list per step.
 
-Multi-GPU (torchrun): every rank runs an independent replica (the state does
-not shard on one-GPU machines); value = all ranks' rotations / max time.
+Multi-GPU (torchrun): every rank runs an independent replica of the workload
+(weak scaling); value = all ranks' rotations / max time.  The global-qubit
+sharded path is timed on one GPU, all its slices on that GPU, as the
+``sharded_one_gpu`` extra.
 """
 from __future__ import annotations
 
