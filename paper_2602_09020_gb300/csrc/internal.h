@@ -17,6 +17,8 @@ constexpr int kMaxDiagRots = 1024;  // rotations per diagonal phase-sum run
 constexpr int kDiagClassBits = 4;   // index bits resolved by the in-thread Walsh-Hadamard step
 constexpr int kDiagClassLo = 5;     // lowest of those bits (above the lane bits)
 constexpr int kDiagMinQubits = kDiagClassLo + kDiagClassBits;
+constexpr int kDiagSlotBits = kDiagClassLo + kDiagClassBits;  // index bits 0..8: lane and class bits
+constexpr int kDiagSlots = 128;  // distinct z patterns on those bits per diagonal run
 constexpr int kMaxExpGroupTerms = 4096;  // terms per expectation run (shared memory)
 constexpr int kThreads = 256;
 
@@ -107,9 +109,13 @@ static_assert(sizeof(RotDev) == 32, "RotDev layout");
 
 // One rotation of a diagonal phase-sum run: a = theta/2 as a fixed-point
 // fraction of a full turn (units of 2 pi / 2^64), plan-frame sign applied.
+// slot = rank of the rotation's z pattern on index bits 0..8 among the run's
+// distinct patterns (the run's rotations are sorted by that pattern).
 struct DiagDev {
   uint64_t z;
   uint64_t a;
+  uint32_t slot;
+  uint32_t pad;
 };
 
 struct RunDev {
@@ -120,7 +126,7 @@ struct RunDev {
   int32_t first, count;   // range in the plan's RotDev or DiagDev array
   int32_t fold;           // multiply by (fold_re + i fold_im) at the end
   double fold_re, fold_im;
-  int32_t seg[(1 << kDiagClassBits) + 1];  // diag runs: rotation ranges per low-bit class
+  int32_t seg[(1 << kDiagClassBits) + 1];  // diag runs: slot ranges per class (z bits 5..8)
 };
 
 // Two consecutive complex64 coset runs applied in one HBM pass (chain.cu).  A

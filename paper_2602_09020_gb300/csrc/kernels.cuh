@@ -559,42 +559,162 @@ __device__ __forceinline__ typename Cx<R>::T turn_phase(uint64_t phi, const type
   return cmul<R>(cmul<R>(t0, t1), s);
 }
 
+// Workspace of body_diag, in this order: phase tables (512 entries, 16-byte
+// aligned for double2), per-rotation angles, per-warp slot sums, per-rotation
+// z-masks, per-slot lane sign masks, per-rotation slots.
 template <typename R, typename Idx>
-__host__ __device__ constexpr size_t ws_diag() {
-  return sizeof(uint64_t) * kMaxDiagRots + sizeof(Idx) * kMaxDiagRots + sizeof(typename Cx<R>::T) * 512;
+__host__ __device__ constexpr size_t ws_diag_off(int part) {
+  size_t off = 0;
+  const size_t sizes[6] = {sizeof(typename Cx<R>::T) * 512, sizeof(uint64_t) * kMaxDiagRots,
+                           sizeof(uint64_t) * kDiagSlots * (kThreads / 32), sizeof(Idx) * kMaxDiagRots,
+                           sizeof(uint32_t) * kDiagSlots, sizeof(uint16_t) * kMaxDiagRots};
+  for (int k = 0; k < part; ++k) off += sizes[k];
+  return off;
 }
 
+template <typename R, typename Idx>
+__host__ __device__ constexpr size_t ws_diag() {
+  return ws_diag_off<R, Idx>(6);
+}
+
+// bit l = parity(l & m) for the 5 lane bits of m
+__device__ __forceinline__ uint32_t lane_signs(uint32_t m) {
+  uint32_t s = 0;
+  if (m & 1u) s ^= 0xAAAAAAAAu;
+  if (m & 2u) s ^= 0xCCCCCCCCu;
+  if (m & 4u) s ^= 0xF0F0F0F0u;
+  if (m & 8u) s ^= 0xFF00FF00u;
+  if (m & 16u) s ^= 0xFFFF0000u;
+  return s;
+}
+
+// A diagonal phase-sum run: amplitude k is multiplied by exp(-i A(k)) with
+// A(k) = sum_j a_j (-1)^{popc(k & z_j)} (a_j = theta_j / 2 in units of 2 pi / 2^64,
+// summed exactly modulo 2^64, so any order gives the same bits).
+//
+// A thread owns a group of 16 amplitudes k = base | (e << 5), e = 0..15 (class
+// bits 5..8), and lane l of a warp has base bits 0..4 = l, so a warp covers
+// index bits 0..8 and shares rest = base bits 9 and up.  With the run's
+// rotations grouped into slots s by their z pattern m_s on bits 0..8 (lane part
+// m_s & 31, class part m_s >> 5),
+//   A(k) = sum_e' (-1)^{popc(e & e')} acc[e'],
+//   acc[e'] = sum_{s : class part e'} (-1)^{popc(l & m_s & 31)} D[s],
+//   D[s] = sum_{j in s} a_j (-1)^{popc(rest & z_j)}.
+// D is warp-uniform: the warp's lanes split the rotations between them (a
+// segmented scan over the slot-sorted rotations, into a warp-private shared
+// array), so a rotation costs each lane a share of a scan step per group
+// instead of a term; a lane then pays one term per slot (a run has at most
+// kDiagSlots of them) and the 16-point transform over the class bits.
+// complex128 instead sums each class's rotations per thread (acc[c] = sum over
+// the rotations of class c of a_j (-1)^{popc(base & z_j)}): there the FP64
+// phase products bound the pass, and they overlap that longer integer work
+// better than the slot sums (measured: 582 against 701 us per pass at n = 24).
+// Needs blockDim.x <= kThreads, a multiple of 32, and n_groups a multiple of 32
+// (n >= 9): every warp then runs whole groups together.
 template <typename R, typename Idx>
 __device__ __forceinline__ void body_diag(typename Cx<R>::T *__restrict__ amp, Idx n_groups, const RunDev &run,
                                           const DiagDev *__restrict__ rots, uint64_t fx,
                                           const typename Cx<R>::T *__restrict__ tab, Idx cta_rank, Idx cta_count,
                                           char *ws) {
+  static_assert(kDiagClassLo == 5, "lane bits 0..4 below the class bits");
   using C = typename Cx<R>::T;
-  uint64_t *sa = (uint64_t *)ws;
-  C *stab = (C *)(ws + sizeof(uint64_t) * kMaxDiagRots);
-  Idx *sz = (Idx *)(ws + sizeof(uint64_t) * kMaxDiagRots + sizeof(C) * 512);
+  C *stab = (C *)(ws + ws_diag_off<R, Idx>(0));
+  uint64_t *sa = (uint64_t *)(ws + ws_diag_off<R, Idx>(1));
+  uint64_t *sD = (uint64_t *)(ws + ws_diag_off<R, Idx>(2));
+  Idx *sz = (Idx *)(ws + ws_diag_off<R, Idx>(3));
+  uint32_t *smask = (uint32_t *)(ws + ws_diag_off<R, Idx>(4));
+  uint16_t *sslot = (uint16_t *)(ws + ws_diag_off<R, Idx>(5));
   const int count = run.count;
+  const int nslots = run.seg[kCls];
   for (int j = threadIdx.x; j < count; j += blockDim.x) {
     const DiagDev r = rots[run.first + j];
     sz[j] = (Idx)r.z;
     sa[j] = (__popcll(r.z & fx) & 1) ? (0ULL - r.a) : r.a;  // runtime frame sign
+    sslot[j] = (uint16_t)r.slot;
+    smask[r.slot] = lane_signs((uint32_t)r.z & 31u);  // the same for every rotation of the slot
   }
   for (int j = threadIdx.x; j < 512; j += blockDim.x) stab[j] = tab[j];
   __syncthreads();
+  // complex128: class c (z bits 5..8) holds rotations [rseg[c], rseg[c + 1])
+  // (the slots, and so the rotations, are sorted by class)
+  __shared__ int rseg[kCls + 1];
+  if constexpr (sizeof(R) == 8) {
+    if (threadIdx.x <= kCls) {
+      const int c = (int)threadIdx.x;
+      int lo = 0, hi = count;  // first rotation of class >= c
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int)((sz[mid] >> kDiagClassLo) & (Idx)(kCls - 1)) < c)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      rseg[c] = lo;
+    }
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31;
+  unsigned long long *D = (unsigned long long *)sD + (threadIdx.x >> 5) * kDiagSlots;
   const Idx stride = cta_count * blockDim.x;
   for (Idx g = cta_rank * blockDim.x + threadIdx.x; g < n_groups; g += stride) {
-    const Idx base = (g & (Idx)((1u << kDiagClassLo) - 1u)) |
-                     ((g >> kDiagClassLo) << (kDiagClassLo + kDiagClassBits));
-    uint64_t acc[kCls];
+    const Idx base = (g & (Idx)31) | ((g >> 5) << (kDiagClassLo + kDiagClassBits));
+    const Idx rest = base & ~(Idx)((1u << (kDiagClassLo + kDiagClassBits)) - 1u);
+    // complex64: the group's amplitudes first, so that their latency overlaps
+    // the sums (16 double2 would cost complex128 its occupancy)
+    constexpr bool kEarly = sizeof(R) == 4;
+    C av[kCls];
+    if (kEarly) {
 #pragma unroll
-    for (int c = 0; c < kCls; ++c) {
-      uint64_t s = 0;
-      const int j1 = run.seg[c + 1];
-      for (int j = run.seg[c]; j < j1; ++j) {
-        const uint64_t a = sa[j];
-        s += parity(base & sz[j]) ? (0ULL - a) : a;
+      for (int e = 0; e < kCls; ++e) av[e] = amp[base | ((Idx)e << kDiagClassLo)];
+    }
+    // D: the warp takes the rotations 32 at a time; they are sorted by slot, so
+    // a segmented scan across the lanes leaves each slot's sum over the batch on
+    // the slot's last lane in it, the one writer of D[s] for that batch
+    uint64_t acc[kCls];
+    if constexpr (sizeof(R) == 8) {
+#pragma unroll
+      for (int c = 0; c < kCls; ++c) {
+        uint64_t t = 0;
+        const int j1 = rseg[c + 1];
+        for (int j = rseg[c]; j < j1; ++j) {
+          const uint64_t a = sa[j];
+          t += parity(base & sz[j]) ? (0ULL - a) : a;
+        }
+        acc[c] = t;
       }
-      acc[c] = s;
+    } else {
+      for (int s = lane; s < nslots; s += 32) D[s] = 0ULL;
+      __syncwarp();
+      for (int j0 = 0; j0 < count; j0 += 32) {
+        const int j = j0 + lane;
+        uint64_t v = 0;
+        int s = -1;
+        if (j < count) {
+          const uint64_t a = sa[j];
+          v = parity(rest & sz[j]) ? (0ULL - a) : a;
+          s = sslot[j];
+        }
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const unsigned long long vu = __shfl_up_sync(0xffffffffu, (unsigned long long)v, off);
+          const int su = __shfl_up_sync(0xffffffffu, s, off);
+          if (lane >= off && su == s) v += vu;
+        }
+        const int sn = __shfl_down_sync(0xffffffffu, s, 1);
+        if (s >= 0 && (lane == 31 || sn != s)) D[s] += v;
+        __syncwarp();
+      }
+#pragma unroll
+      for (int c = 0; c < kCls; ++c) {
+        uint64_t t = 0;
+        const int s1 = run.seg[c + 1];
+        for (int s = run.seg[c]; s < s1; ++s) {
+          const uint64_t d = D[s];
+          t += ((smask[s] >> lane) & 1u) ? (0ULL - d) : d;
+        }
+        acc[c] = t;
+      }
+      __syncwarp();  // D is cleared for the next group
     }
     // acc[e] <- sum_c (-1)^{popc(e & c)} acc[c]
 #pragma unroll
@@ -616,7 +736,7 @@ __device__ __forceinline__ void body_diag(typename Cx<R>::T *__restrict__ amp, I
         f.y = (R)run.fold_im;
         ph = cmul<R>(ph, f);
       }
-      amp[k] = cmul<R>(amp[k], ph);
+      amp[k] = cmul<R>(kEarly ? av[e] : amp[k], ph);
     }
   }
   __syncthreads();  // the workspace may be reused by the caller's next pass

@@ -225,9 +225,23 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
     if (in_diag[k]) {
       rc = finish_coset_run(false);
       if (rc) return rc;
+      // one phase-sum run over items[k, b) (all diagonal, so any order is
+      // exact), cut at kMaxDiagRots rotations or kDiagSlots distinct patterns
+      // of index bits 0..8 in the z-masks
       size_t b = k;
-      while (b < items.size() && in_diag[b] && b - k < (size_t)kMaxDiagRots) ++b;
-      // one phase-sum run over items[k, b); all diagonal, so any order is exact
+      {
+        bool seen[1 << kDiagSlotBits] = {};
+        int distinct = 0;
+        while (b < items.size() && in_diag[b] && b - k < (size_t)kMaxDiagRots) {
+          const int m = (int)(items[b].z & ((1u << kDiagSlotBits) - 1));
+          if (!seen[m]) {
+            if (distinct == kDiagSlots) break;
+            seen[m] = true;
+            ++distinct;
+          }
+          ++b;
+        }
+      }
       std::vector<DiagDev> chunk;
       std::vector<int> cls;
       for (size_t m = k; m < b; ++m) {
@@ -236,15 +250,18 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
         DiagDev dd;
         dd.z = it.z;
         dd.a = fixed_half_angle(sp * it.theta);
+        dd.slot = 0;
+        dd.pad = 0;
         chunk.push_back(dd);
-        cls.push_back((int)((it.z >> kDiagClassLo) & ((1u << kDiagClassBits) - 1)));
+        // sort key: the z pattern on index bits 0..8, class bits 5..8 first
+        cls.push_back((int)(it.z & ((1u << kDiagSlotBits) - 1)));
         p->order.push_back(it.idx);
         p->beta.push_back(sp * it.theta);
         p->sigma.push_back((int8_t)sp);
         p->ox.push_back(it.x);
         p->oz.push_back(it.z);
       }
-      // stable sort by class; the adjoint order follows the device order
+      // stable sort by pattern; the adjoint order follows the device order
       std::vector<size_t> perm(chunk.size());
       for (size_t m = 0; m < perm.size(); ++m) perm[m] = m;
       std::stable_sort(perm.begin(), perm.end(), [&](size_t a1, size_t b1) { return cls[a1] < cls[b1]; });
@@ -258,11 +275,18 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
       r.kind = 1;
       r.first = (int32_t)diags.size();
       r.count = (int32_t)chunk.size();
-      int cur = 0;
+      // slots: the distinct patterns in sorted order; seg[c] = first slot of
+      // class c (pattern bits 5..8), seg[16] = number of slots
+      int cur = 0, slot = -1, last = -1;
       r.seg[0] = 0;
       for (size_t m = 0; m < perm.size(); ++m) {
         size_t src = perm[m];
-        while (cur < cls[src]) r.seg[++cur] = (int32_t)m;
+        if (cls[src] != last) {
+          ++slot;
+          last = cls[src];
+          while (cur < (cls[src] >> kDiagClassLo)) r.seg[++cur] = (int32_t)slot;
+        }
+        chunk[src].slot = (uint32_t)slot;
         diags.push_back(chunk[src]);
         o2[m] = p->order[base_order + src];
         b2[m] = p->beta[base_order + src];
@@ -270,7 +294,7 @@ int build_plan(sv_plan *p, int n, int dtype, const uint64_t *x, const uint64_t *
         x2[m] = p->ox[base_order + src];
         z2[m] = p->oz[base_order + src];
       }
-      while (cur < (1 << kDiagClassBits)) r.seg[++cur] = (int32_t)perm.size();
+      while (cur < (1 << kDiagClassBits)) r.seg[++cur] = (int32_t)(slot + 1);
       for (size_t m = 0; m < perm.size(); ++m) {
         p->order[base_order + m] = o2[m];
         p->beta[base_order + m] = b2[m];

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <typename R, typename Idx>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
     k_diag_sum(typename Cx<R>::T *__restrict__ amp, Idx n_groups, const __grid_constant__ RunDev run,
                const DiagDev *__restrict__ rots, uint64_t fx, const typename Cx<R>::T *__restrict__ tab) {
   __shared__ __align__(16) char ws[ws_diag<R, Idx>()];
@@ -284,6 +284,8 @@ int launch_run(sv_state *sv, const sv_plan *plan, const RunDev &run, uint64_t fx
   const bool narrow = sv->n <= 31;
   if (run.kind == 1) {
     if (sv->n < kDiagMinQubits) return fail(SV_EINVAL, "diagonal run needs n >= %d", kDiagMinQubits);
+    if (run.count > kMaxDiagRots || run.seg[1 << kDiagClassBits] > kDiagSlots)
+      return fail(SV_EINVAL, "diagonal run exceeds %d rotations or %d z patterns", kMaxDiagRots, kDiagSlots);
     if (sv->dtype == SV_C128)
       return narrow ? launch_diag_t<double, uint32_t>(sv, plan, run, fx)
                     : launch_diag_t<double, uint64_t>(sv, plan, run, fx);

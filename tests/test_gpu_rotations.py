@@ -98,6 +98,35 @@ def test_diagonal_phase_sum_runs(orc, n):
     assert_close_c64(want, got64, what=f"c64 diag n={n}", atol=2e-4)
 
 
+@pytest.mark.parametrize("kind", ["distinct", "zz"])
+def test_diagonal_runs_cut_at_the_pattern_cap(orc, kind):
+    # a diagonal run holds at most 128 distinct z patterns on index bits 0..8
+    # (its rotations are grouped by pattern); longer stretches become several runs
+    n = 12
+    g = np.random.default_rng(21)
+    if kind == "distinct":
+        count = 400
+        z = np.array([(j % 511) + 1 + (int(g.integers(0, 8)) << 9) for j in range(count)], dtype=np.uint64)
+        want_runs = 4
+    else:  # every Z_p and Z_p Z_q, as in a Jordan-Wigner Hamiltonian's number terms
+        z = [1 << p for p in range(n)] + [(1 << p) | (1 << q) for p in range(n) for q in range(p + 1, n)]
+        z = np.array(z, dtype=np.uint64)
+        count = len(z)
+        want_runs = 1
+    x = np.zeros(count, dtype=np.uint64)
+    th = g.uniform(-5, 5, size=count)
+    psi0 = synth.random_state(n, 4)
+    p = capi.plan_create(n, "c128", x, z, th, -1)
+    _, nruns, ndiag = capi.plan_stats(p)
+    capi.plan_free(p)
+    assert ndiag == nruns == want_runs
+    want = run_oracle(orc, n, psi0, x, z, th)
+    got, _ = run_gpu(n, "c128", psi0, x, z, th)
+    assert_close_c128(want, got, what=f"diag {kind}")
+    got64, _ = run_gpu(n, "c64", psi0.astype(np.complex64), x, z, th)
+    assert_close_c64(want, got64, what=f"c64 diag {kind}", atol=2e-4)
+
+
 def test_identity_strings_are_global_phase(orc):
     n = 6
     psi0 = synth.random_state(n, 1)
