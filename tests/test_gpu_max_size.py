@@ -6,7 +6,11 @@ ones; the other qubits hold fixed bits, and some z-masks reach one of them, so
 those rotations pick up the sign of its bit.  The state therefore stays
 |fixed> (x) |12-qubit state>, whose 4096 amplitudes are gathered on the device
 and compared with the oracle at n = 12 (qubit j of the oracle = active[j]),
-together with <H> of a Hamiltonian on the same register.
+together with <H> of a Hamiltonian on the same register.  The list holds a
+stretch of Z / ZZ strings (a diagonal phase-sum run) between random strings,
+and Pauli gates on the register go into the frame first (the oracle applies
+them as gates); the launch trace shows the diagonal pass and, for complex64,
+the two-run pass ran.
 """
 import numpy as np
 import pytest
@@ -37,6 +41,12 @@ def test_maximum_size_register_against_oracle(orc, n, dtype):
     xo = rng.integers(0, 1 << m, size=count)
     xo[rng.random(count) < 0.2] = 0  # some diagonal rotations
     zo = rng.integers(0, 1 << m, size=count)
+    # a diagonal stretch in the middle: every Z_j and Z_j Z_{j+1} on the register
+    zd = [1 << j for j in range(m)] + [(3 << j) for j in range(m - 1)]
+    half = count // 2
+    xo = np.concatenate([xo[:half], np.zeros(len(zd), dtype=xo.dtype), xo[half:]])
+    zo = np.concatenate([zo[:half], np.array(zd, dtype=zo.dtype), zo[half:]])
+    count = len(xo)
     th = rng.uniform(-3, 3, size=count)
     touch = rng.random(count) < 0.5
     X = np.array([embed(int(v), active) for v in xo], dtype=np.uint64)
@@ -49,7 +59,10 @@ def test_maximum_size_register_against_oracle(orc, n, dtype):
     HX = np.array([embed(int(v), active) for v in hx], dtype=np.uint64)
     HZ = np.array([embed(int(v), active) for v in hz], dtype=np.uint64)
 
+    gates = [("X", m - 1), ("Z", m - 3), ("Y", 0), ("X", m - 2)]  # (Pauli, register qubit)
     psi = orc.basis_state(m, b0)
+    for p, j in gates:
+        orc.gate(psi, m, p.lower(), j)
     orc.apply_rotations(psi, m, xo.astype(np.uint64), zo.astype(np.uint64), th_oracle)
     e_ref = orc.expval(psi, m, hx.astype(np.uint64), hz.astype(np.uint64), hc)
 
@@ -59,7 +72,11 @@ def test_maximum_size_register_against_oracle(orc, n, dtype):
     sv = capi.sv_wrap(t.data_ptr(), n, dtype, stream)
     try:
         capi.sv_set_basis_state(sv, fixed | embed(b0, active))
+        for p, j in gates:
+            capi.frame_apply_pauli(sv, p, active[j])
+        capi.sv_trace_start(sv)
         capi.apply_pauli_rotations(sv, X, Z, th)
+        rows = capi.sv_trace_stop(sv)
         e, nrm = capi.expval_pauli_sum(sv, HX, HZ, hc)
         capi.sv_materialize(sv)
         torch.cuda.synchronize()
@@ -69,6 +86,9 @@ def test_maximum_size_register_against_oracle(orc, n, dtype):
         capi.sv_free(sv)
         del t
         torch.cuda.empty_cache()
+    assert rows.get("k_diag_sum", (0,))[0] >= 1, rows
+    if dtype == "c64":
+        assert rows.get("k_chain2", (0,))[0] >= 1, rows
     # nothing leaked outside the register: its amplitudes carry the whole norm
     assert abs(nrm - float(np.vdot(got, got).real)) <= (1e-12 if dtype == "c128" else 1e-5)
     if dtype == "c128":
