@@ -256,7 +256,9 @@ int plan_tune_cache_save(const char *path);
  * rotations in list order, identity strings left out: run i holds the next
  * runs[i].count of them.  kind 0 = fused coset run (one pass; its x-masks
  * lie in the span of basis[0..d-1], a reduced basis whose vectors' highest set
- * bits are distinct), kind 1 = diagonal phase-sum run (x = 0 only; d = 0).  A
+ * bits are distinct), kind 1 = diagonal phase-sum run (x = 0 only; d = 0; at
+ * most 1024 rotations and 128 distinct z patterns on index bits 0..8, so a
+ * longer stretch of diagonal rotations becomes several runs).  A
  * run may hold no rotation when it only folds the running scale.  At most cap
  * runs are written; *out_runs (nullable) = all runs, *out_rotations (nullable)
  * = rotations after dropping identities. */
