@@ -88,6 +88,21 @@ def test_long_diagonal_stretches_get_their_own_runs():
     assert all(k == 0 for k, *_ in runs)
 
 
+def test_diagonal_runs_hold_at_most_128_low_bit_patterns():
+    # the diagonal kernel groups a run's rotations by their z pattern on index
+    # bits 0..8; a stretch with more distinct patterns is cut into several runs
+    n = 12
+    g = np.random.default_rng(4)
+    z = np.array([(j % 511) + 1 + (int(g.integers(0, 8)) << 9) for j in range(400)], dtype=np.uint64)
+    x = np.zeros(400, dtype=np.uint64)
+    runs, _ = capi.plan_inspect(n, "c64", x, z, np.full(400, 0.3), 4)
+    assert [(k, c) for k, _, c, _ in runs] == [(1, 128), (1, 128), (1, 128), (1, 16)]
+    # the same count of rotations on few patterns stays one run, up to 1024 rotations
+    z2 = np.array([1 << (j % 12) for j in range(1100)], dtype=np.uint64)
+    runs, _ = capi.plan_inspect(n, "c64", np.zeros(1100, dtype=np.uint64), z2, np.full(1100, 0.3), 4)
+    assert [(k, c) for k, _, c, _ in runs] == [(1, 1024), (1, 76)]
+
+
 def test_run_length_is_capped():
     n = 10
     x = np.full(1000, 6, dtype=np.uint64)
